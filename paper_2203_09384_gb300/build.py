@@ -1,0 +1,92 @@
+"""In-tree build of libgbfft.so for sm_103a (nvcc, no cmake).
+
+The kernels are compiled once per transform length (``-DGBFFT_LOG2N=k``) in
+parallel, then linked with the host plan code into one shared library with
+the CUDA runtime linked statically.  Outputs go to ``_build/`` beside this
+file (git-ignored).  ``python -m paper_2203_09384_gb300.build`` runs it.
+"""
+from __future__ import annotations
+
+import concurrent.futures as cf
+import os
+import shutil
+import subprocess
+import sys
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+CSRC = os.path.join(HERE, "csrc")
+BUILD = os.path.join(HERE, "_build")
+LIB = os.path.join(BUILD, "libgbfft.so")
+ROOT = os.path.dirname(HERE)
+INCLUDE = os.path.join(ROOT, "include")
+
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+CFLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
+          "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]
+LOG2NS = range(1, 12)
+
+
+def nvcc() -> str:
+    cand = os.environ.get("NVCC") or shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(cand) and shutil.which(cand) is None:
+        raise RuntimeError("nvcc not found: the CUDA toolkit is required to build libgbfft.so")
+    return cand
+
+
+def _sources():
+    deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
+    deps.append(os.path.join(INCLUDE, "gbfft.h"))
+    units = [(os.path.join(CSRC, "fft_kernels.cu"), f"fft_kernels_{k}.o", [f"-DGBFFT_LOG2N={k}"])
+             for k in LOG2NS]
+    units.append((os.path.join(CSRC, "gbfft_host.cu"), "gbfft_host.o", []))
+    return units, deps
+
+
+def _stale(target, inputs):
+    if not os.path.exists(target):
+        return True
+    t = os.path.getmtime(target)
+    return any(os.path.getmtime(i) > t for i in inputs)
+
+
+def _compile(src, obj, defs, deps, verbose):
+    out = os.path.join(BUILD, "obj", obj)
+    if not _stale(out, [src] + deps):
+        return out, False
+    cmd = [nvcc(), *ARCH, *CFLAGS, *defs, "-c", src, "-o", out + ".tmp"]
+    if verbose:
+        cmd.insert(1, "-Xptxas=-v")
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"nvcc failed on {os.path.basename(src)} {' '.join(defs)}:\n{r.stdout}\n{r.stderr}")
+    if verbose and r.stderr:
+        sys.stderr.write(r.stderr)
+    os.replace(out + ".tmp", out)
+    return out, True
+
+
+def build(jobs: int | None = None, verbose: bool = False, force: bool = False) -> str:
+    """Compile every kernel unit and link ``_build/libgbfft.so``; returns its path."""
+    os.makedirs(os.path.join(BUILD, "obj"), exist_ok=True)
+    units, deps = _sources()
+    if force:
+        for _, obj, _ in units:
+            p = os.path.join(BUILD, "obj", obj)
+            if os.path.exists(p):
+                os.remove(p)
+    jobs = jobs or min(len(units), os.cpu_count() or 4)
+    with cf.ThreadPoolExecutor(max_workers=jobs) as ex:
+        results = list(ex.map(lambda u: _compile(u[0], u[1], u[2], deps, verbose), units))
+    objs = [r[0] for r in results]
+    if any(r[1] for r in results) or _stale(LIB, objs):
+        tmp = LIB + f".tmp{os.getpid()}"
+        cmd = [nvcc(), *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
+        os.replace(tmp, LIB)
+    return LIB
+
+
+if __name__ == "__main__":
+    print(build(verbose="-v" in sys.argv, force="--force" in sys.argv))

@@ -1,0 +1,417 @@
+// Device code of the batched FP32 C2C power-of-two FFT (sm_103a).
+//
+// The transform is Eq. (dft) of Pascuzzi & Goli (Sec. 3); the inverse,
+// Eq. (idft), is taken as conj(DFT(conj(x))) times 1/N, so one forward
+// butterfly set and one twiddle table serve both directions.
+//
+// Algorithm: Stockham autosort decimation in time, mixed radix 2/4/8/16
+// (Sec. 3.1 radix-2 split generalised to the higher radices the paper's
+// Sec. 4 lists).  With stage radices R_0..R_{M-1} and Ns = R_0*...*R_{s-1},
+// stage s performs N/R butterflies; butterfly j
+//   reads   a_r = x[j + r*N/R]                                (r < R)
+//   twists  a_r *= omega_{Ns*R}^{(j mod Ns)*r}
+//   applies the R-point DFT  b_q = sum_r a_r omega_R^{rq}
+//   writes  y[(j div Ns)*Ns*R + (j mod Ns) + q*Ns] = b_q      (q < R)
+// and the last stage leaves the result in natural order (no bit reversal).
+//
+// GB300 mapping: each thread keeps E complex elements in registers and runs
+// E/R butterflies per stage.  Stage 0 reads straight from HBM and the last
+// stage writes straight to HBM, with 128-bit accesses whenever a thread owns
+// two neighbouring butterflies; stages exchange through shared memory with an
+// XOR swizzle that makes every exchange bank-conflict free.  A persistent
+// grid-stride loop walks tiles of S signals.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace gbfft {
+
+// ---------------------------------------------------------------------------
+// complex helpers (float2 = interleaved complex64)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 w) {
+    return make_float2(a.x * w.x - a.y * w.y, a.x * w.y + a.y * w.x);
+}
+// (x + iy) * (-i) = y - ix
+__device__ __forceinline__ float2 mul_neg_i(float2 a) { return make_float2(a.y, -a.x); }
+__device__ __forceinline__ float2 conj2(float2 a) { return make_float2(a.x, -a.y); }
+
+// Roots of unity used inside the radix-8 and radix-16 butterflies:
+// cos(pi/4), cos(pi/8), sin(pi/8).
+constexpr float kSqrtHalf = 0.70710678118654752440f;
+constexpr float kCos8 = 0.92387953251128675613f;
+constexpr float kSin8 = 0.38268343236508977173f;
+
+// omega_8 * a = sqrt(1/2) (1 - i) a
+__device__ __forceinline__ float2 mul_w8_1(float2 a) {
+    return make_float2(kSqrtHalf * (a.x + a.y), kSqrtHalf * (a.y - a.x));
+}
+// omega_8^3 * a = sqrt(1/2) (-1 - i) a
+__device__ __forceinline__ float2 mul_w8_3(float2 a) {
+    return make_float2(kSqrtHalf * (a.y - a.x), -kSqrtHalf * (a.x + a.y));
+}
+
+// ---------------------------------------------------------------------------
+// R-point DFTs in registers, in place, natural order in and out:
+// v[q] <- sum_r v[r] omega_R^{rq}, omega_R = e^{-2 pi i / R}.
+// ---------------------------------------------------------------------------
+template <int R>
+struct Dft;
+
+template <>
+struct Dft<1> {
+    static __device__ __forceinline__ void run(float2*) {}
+};
+
+template <>
+struct Dft<2> {
+    static __device__ __forceinline__ void run(float2* v) {
+        float2 a = v[0], b = v[1];
+        v[0] = cadd(a, b);
+        v[1] = csub(a, b);
+    }
+};
+
+template <>
+struct Dft<4> {
+    static __device__ __forceinline__ void run(float2* v) {
+        float2 s02 = cadd(v[0], v[2]), d02 = csub(v[0], v[2]);
+        float2 s13 = cadd(v[1], v[3]), d13 = mul_neg_i(csub(v[1], v[3]));
+        v[0] = cadd(s02, s13);
+        v[2] = csub(s02, s13);
+        v[1] = cadd(d02, d13);
+        v[3] = csub(d02, d13);
+    }
+};
+
+template <>
+struct Dft<8> {
+    // radix-2 split (Eq. (radix2)) over two 4-point DFTs
+    static __device__ __forceinline__ void run(float2* v) {
+        float2 e[4] = {v[0], v[2], v[4], v[6]};
+        float2 o[4] = {v[1], v[3], v[5], v[7]};
+        Dft<4>::run(e);
+        Dft<4>::run(o);
+        o[1] = mul_w8_1(o[1]);
+        o[2] = mul_neg_i(o[2]);
+        o[3] = mul_w8_3(o[3]);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            v[k] = cadd(e[k], o[k]);
+            v[k + 4] = csub(e[k], o[k]);
+        }
+    }
+};
+
+template <>
+struct Dft<16> {
+    // 4 x 4: input index r1 + 4 r2, output index k2 + 4 k1.
+    static __device__ __forceinline__ void run(float2* v) {
+        float2 y[4][4];
+#pragma unroll
+        for (int r1 = 0; r1 < 4; ++r1) {
+            y[r1][0] = v[r1];
+            y[r1][1] = v[r1 + 4];
+            y[r1][2] = v[r1 + 8];
+            y[r1][3] = v[r1 + 12];
+            Dft<4>::run(y[r1]);
+        }
+        // twiddles omega_16^{r1 k2}
+        y[1][1] = cmul(y[1][1], make_float2(kCos8, -kSin8));         // ^1
+        y[1][2] = mul_w8_1(y[1][2]);                                 // ^2
+        y[1][3] = cmul(y[1][3], make_float2(kSin8, -kCos8));         // ^3
+        y[2][1] = mul_w8_1(y[2][1]);                                 // ^2
+        y[2][2] = mul_neg_i(y[2][2]);                                // ^4
+        y[2][3] = mul_w8_3(y[2][3]);                                 // ^6
+        y[3][1] = cmul(y[3][1], make_float2(kSin8, -kCos8));         // ^3
+        y[3][2] = mul_w8_3(y[3][2]);                                 // ^6
+        y[3][3] = cmul(y[3][3], make_float2(-kCos8, kSin8));         // ^9
+#pragma unroll
+        for (int k2 = 0; k2 < 4; ++k2) {
+            float2 z[4] = {y[0][k2], y[1][k2], y[2][k2], y[3][k2]};
+            Dft<4>::run(z);
+#pragma unroll
+            for (int k1 = 0; k1 < 4; ++k1) v[k2 + 4 * k1] = z[k1];
+        }
+    }
+};
+
+// ---------------------------------------------------------------------------
+// memory helpers: streaming (evict-first) 64/128-bit global accesses
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float4 ld_stream4(const float2* p) { return __ldcs(reinterpret_cast<const float4*>(p)); }
+__device__ __forceinline__ float2 ld_stream2(const float2* p) { return __ldcs(p); }
+__device__ __forceinline__ void st_stream4(float2* p, float2 a, float2 b) {
+    __stcs(reinterpret_cast<float4*>(p), make_float4(a.x, a.y, b.x, b.y));
+}
+__device__ __forceinline__ void st_stream2(float2* p, float2 a) { __stcs(p, a); }
+
+// Shared-memory swizzle at 8-byte granularity: rows of 16 elements (128 B)
+// are XOR-permuted by their row index.  Keeps every Stockham exchange of the
+// schedules below conflict free (checked by an index model on the host).
+__device__ __forceinline__ int swz8(int a) { return a ^ ((a >> 4) & 15); }
+// Same idea at 16-byte granularity (rows of 8 float4 slots).
+__device__ __forceinline__ int swz16(int a) { return a ^ ((a >> 3) & 7); }
+
+// ---------------------------------------------------------------------------
+// Compile-time schedule
+// ---------------------------------------------------------------------------
+template <int LOG2N_, int E_, int S_, int R0, int R1, int R2, int R3>
+struct Cfg {
+    static constexpr int LOG2N = LOG2N_;
+    static constexpr int N = 1 << LOG2N_;
+    static constexpr int E = E_;          // complex elements per thread
+    static constexpr int S = S_;          // signals per tile (per block)
+    static constexpr int T = N / E;       // threads per signal
+    static constexpr int NT = T * S;      // threads per block
+    static constexpr int M = (R0 > 0) + (R1 > 0) + (R2 > 0) + (R3 > 0);
+    static constexpr bool kWarpLocal = T <= 32;  // a signal never spans warps
+    static constexpr int kBuffers = kWarpLocal ? 1 : 2;
+    static constexpr int kSmemElems = kBuffers * S * N;
+    __host__ __device__ static constexpr int radix(int s) {
+        return s == 0 ? R0 : s == 1 ? R1 : s == 2 ? R2 : R3;
+    }
+    // Ns of stage s: product of the radices before it
+    __host__ __device__ static constexpr int ns(int s) {
+        int p = 1;
+        for (int i = 0; i < s; ++i) p *= radix(i);
+        return p;
+    }
+    // offset of stage s's twiddles: (R_i - 1) * Ns_i entries for each i in [1, s)
+    __host__ __device__ static constexpr int tw_off(int s) {
+        int o = 0;
+        for (int i = 1; i < s; ++i) o += (radix(i) - 1) * ns(i);
+        return o;
+    }
+    static constexpr int kTwiddles = tw_off(M);
+    static_assert(N % E == 0, "E must divide N");
+    static_assert(ns(M) == N, "radices must multiply to N");
+    static_assert(M >= 2, "generic kernel needs at least two stages");
+    static_assert(E % R0 == 0 && (R1 == 0 || E % R1 == 0) && (R2 == 0 || E % R2 == 0) &&
+                      (R3 == 0 || E % R3 == 0),
+                  "every radix must divide E");
+    static_assert(32 % T == 0 || T % 32 == 0, "T must tile warps");
+};
+
+// Butterfly handled by thread t in slot c of stage s.  The first and the last
+// stage give a thread neighbouring butterflies (vectorised HBM access); the
+// middle stages interleave threads (coalesced, conflict-free exchanges).
+template <class C, int s>
+__device__ __forceinline__ int bfly(int t, int c) {
+    constexpr int K = C::E / C::radix(s);
+    if constexpr (s == 0 || s == C::M - 1) {
+        return K * t + c;
+    } else {
+        return t + C::T * c;
+    }
+}
+
+template <class C, int s>
+__device__ __forceinline__ void twist_and_dft(float2 (&v)[C::E], int t, const float2* __restrict__ tw) {
+    constexpr int R = C::radix(s);
+    constexpr int K = C::E / R;
+    constexpr int Ns = C::ns(s);
+#pragma unroll
+    for (int c = 0; c < K; ++c) {
+        if constexpr (s > 0) {
+            const int j = bfly<C, s>(t, c);
+            const float2* twp = tw + C::tw_off(s) + (j & (Ns - 1));
+#pragma unroll
+            for (int r = 1; r < R; ++r) v[c * R + r] = cmul(v[c * R + r], __ldg(twp + (r - 1) * Ns));
+        }
+        Dft<R>::run(&v[c * R]);
+    }
+}
+
+// stage s outputs -> shared memory (signal base `sb` within the block's buffer)
+template <class C, int s>
+__device__ __forceinline__ void scatter(const float2 (&v)[C::E], float2* buf, int sb, int t) {
+    constexpr int R = C::radix(s);
+    constexpr int K = C::E / R;
+    constexpr int Ns = C::ns(s);
+#pragma unroll
+    for (int c = 0; c < K; ++c) {
+        const int j = bfly<C, s>(t, c);
+        const int base = sb + (j / Ns) * (Ns * R) + (j & (Ns - 1));
+#pragma unroll
+        for (int q = 0; q < R; ++q) buf[swz8(base + q * Ns)] = v[c * R + q];
+    }
+}
+
+// shared memory -> stage s inputs
+template <class C, int s>
+__device__ __forceinline__ void gather(float2 (&v)[C::E], const float2* buf, int sb, int t) {
+    constexpr int R = C::radix(s);
+    constexpr int K = C::E / R;
+    constexpr int stride = C::N / R;
+#pragma unroll
+    for (int c = 0; c < K; ++c) {
+        const int j = bfly<C, s>(t, c);
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[c * R + r] = buf[swz8(sb + j + r * stride)];
+    }
+}
+
+// stage 0 inputs straight from HBM
+template <class C, bool INV>
+__device__ __forceinline__ void load_first(float2 (&v)[C::E], const float2* src, int t, bool active) {
+    constexpr int R = C::radix(0);
+    constexpr int K = C::E / R;
+    constexpr int stride = C::N / R;
+    if (!active) {
+#pragma unroll
+        for (int i = 0; i < C::E; ++i) v[i] = make_float2(0.f, 0.f);
+        return;
+    }
+    if constexpr (K >= 2) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+#pragma unroll
+            for (int c = 0; c < K; c += 2) {
+                float4 f = ld_stream4(src + K * t + c + r * stride);
+                v[c * R + r] = make_float2(f.x, f.y);
+                v[(c + 1) * R + r] = make_float2(f.z, f.w);
+            }
+        }
+    } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = ld_stream2(src + t + r * stride);
+    }
+    if constexpr (INV) {
+#pragma unroll
+        for (int i = 0; i < C::E; ++i) v[i].y = -v[i].y;
+    }
+}
+
+// last-stage outputs straight to HBM (natural order)
+template <class C, bool INV>
+__device__ __forceinline__ void store_last(float2 (&v)[C::E], float2* dst, int t, bool active, float scale) {
+    constexpr int R = C::radix(C::M - 1);
+    constexpr int K = C::E / R;
+    constexpr int stride = C::N / R;
+    if (!active) return;
+#pragma unroll
+    for (int i = 0; i < C::E; ++i) v[i] = make_float2(v[i].x * scale, (INV ? -v[i].y : v[i].y) * scale);
+    if constexpr (K >= 2) {
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+#pragma unroll
+            for (int c = 0; c < K; c += 2) st_stream4(dst + K * t + c + q * stride, v[c * R + q], v[(c + 1) * R + q]);
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < R; ++q) st_stream2(dst + t + q * stride, v[q]);
+    }
+}
+
+template <class C>
+__device__ __forceinline__ void exchange_barrier() {
+    if constexpr (C::kWarpLocal) {
+        __syncwarp();
+    } else {
+        __syncthreads();
+    }
+}
+
+// stages 1..M-1: exchange through shared memory, then butterflies
+template <class C, int s>
+__device__ __forceinline__ void rest_stages(float2 (&v)[C::E], float2* smem, int& buf, int sb, int t,
+                                            const float2* __restrict__ tw) {
+    if constexpr (s < C::M) {
+        float2* b = smem + buf * (C::S * C::N);
+        if constexpr (C::kWarpLocal) __syncwarp();  // previous readers of b are done
+        scatter<C, s - 1>(v, b, sb, t);
+        exchange_barrier<C>();
+        gather<C, s>(v, b, sb, t);
+        if constexpr (C::kBuffers == 2) buf ^= 1;
+        twist_and_dft<C, s>(v, t, tw);
+        rest_stages<C, s + 1>(v, smem, buf, sb, t, tw);
+    }
+}
+
+// The generic kernel: N = 32..2048.
+template <class C, bool INV>
+__global__ void __launch_bounds__(C::NT) fft_stockham_kernel(const float2* in, float2* out, int64_t batch,
+                                                             const float2* __restrict__ tw, float scale) {
+    extern __shared__ __align__(16) float2 smem[];
+    const int tid = threadIdx.x;
+    const int sl = tid / C::T;
+    const int t = tid % C::T;
+    const int sb = sl * C::N;
+    const int64_t ntiles = (batch + C::S - 1) / C::S;
+    int buf = 0;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t sig = tile * C::S + sl;
+        const bool active = sig < batch;
+        const int64_t base = sig * C::N;
+        float2 v[C::E];
+        load_first<C, INV>(v, in + base, t, active);
+        twist_and_dft<C, 0>(v, t, tw);
+        rest_stages<C, 1>(v, smem, buf, sb, t, tw);
+        store_last<C, INV>(v, out + base, t, active, scale);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// N = 2..16: one thread owns a whole signal.  Each warp stages a contiguous
+// tile of 32 signals through shared memory with coalesced 128-bit copies, so
+// HBM sees fully used sectors while each thread reads its own signal.
+// ---------------------------------------------------------------------------
+constexpr int kSmallWarps = 8;
+
+template <int LOG2N>
+struct SmallCfg {
+    static constexpr int N = 1 << LOG2N;
+    static constexpr int H = N / 2;  // float4 slots per signal
+    static constexpr int NT = 32 * kSmallWarps;
+    static constexpr int kSmemBytes = kSmallWarps * 32 * H * 16;
+};
+
+template <int LOG2N, bool INV>
+__global__ void __launch_bounds__(SmallCfg<LOG2N>::NT) fft_small_kernel(const float2* in, float2* out, int64_t batch,
+                                                                        float scale) {
+    using C = SmallCfg<LOG2N>;
+    constexpr int N = C::N, H = C::H;
+    extern __shared__ __align__(16) float4 smem4[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float4* sm = smem4 + warp * (32 * H);
+    const int64_t wtiles = (batch + 31) / 32;
+    for (int64_t wt = (int64_t)blockIdx.x * kSmallWarps + warp; wt < wtiles; wt += (int64_t)gridDim.x * kSmallWarps) {
+        const int64_t first = wt * 32;
+        const int64_t left = batch - first;
+        const int valid4 = (int)((left < 32 ? left : 32) * H);
+        const float4* src = reinterpret_cast<const float4*>(in + first * N);
+        float4* dst = reinterpret_cast<float4*>(out + first * N);
+#pragma unroll
+        for (int i = 0; i < H; ++i) {
+            const int p = lane + 32 * i;
+            if (p < valid4) sm[swz16(p)] = __ldcs(src + p);
+        }
+        __syncwarp();
+        float2 v[N];
+#pragma unroll
+        for (int i = 0; i < H; ++i) {
+            float4 f = sm[swz16(lane * H + i)];
+            v[2 * i] = make_float2(f.x, INV ? -f.y : f.y);
+            v[2 * i + 1] = make_float2(f.z, INV ? -f.w : f.w);
+        }
+        Dft<N>::run(v);
+#pragma unroll
+        for (int i = 0; i < N; ++i) v[i] = make_float2(v[i].x * scale, (INV ? -v[i].y : v[i].y) * scale);
+#pragma unroll
+        for (int i = 0; i < H; ++i)
+            sm[swz16(lane * H + i)] = make_float4(v[2 * i].x, v[2 * i].y, v[2 * i + 1].x, v[2 * i + 1].y);
+        __syncwarp();
+#pragma unroll
+        for (int i = 0; i < H; ++i) {
+            const int p = lane + 32 * i;
+            if (p < valid4) __stcs(dst + p, sm[swz16(p)]);
+        }
+        __syncwarp();
+    }
+}
+
+}  // namespace gbfft

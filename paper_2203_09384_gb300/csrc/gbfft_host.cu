@@ -1,0 +1,334 @@
+// Host side of the C-ABI: argument validation, plan construction (radix
+// schedule lookup, FP64 twiddle generation rounded to FP32, launch shape),
+// asynchronous execution and error reporting.  See include/gbfft.h.
+#include <cuda_runtime.h>
+
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <mutex>
+#include <new>
+
+#include "../../include/gbfft.h"
+#include "registry.h"
+#include "schedules.h"
+
+GBFFT_DECLARE_ENTRY(1)
+GBFFT_DECLARE_ENTRY(2)
+GBFFT_DECLARE_ENTRY(3)
+GBFFT_DECLARE_ENTRY(4)
+GBFFT_DECLARE_ENTRY(5)
+GBFFT_DECLARE_ENTRY(6)
+GBFFT_DECLARE_ENTRY(7)
+GBFFT_DECLARE_ENTRY(8)
+GBFFT_DECLARE_ENTRY(9)
+GBFFT_DECLARE_ENTRY(10)
+GBFFT_DECLARE_ENTRY(11)
+
+namespace {
+
+using gbfft::KernelEntry;
+
+const KernelEntry* registry() {
+    static KernelEntry table[GBFFT_MAX_LOG2N + 1];
+    static std::once_flag once;
+    std::call_once(once, [] {
+        table[1] = gbfft_entry_1();
+        table[2] = gbfft_entry_2();
+        table[3] = gbfft_entry_3();
+        table[4] = gbfft_entry_4();
+        table[5] = gbfft_entry_5();
+        table[6] = gbfft_entry_6();
+        table[7] = gbfft_entry_7();
+        table[8] = gbfft_entry_8();
+        table[9] = gbfft_entry_9();
+        table[10] = gbfft_entry_10();
+        table[11] = gbfft_entry_11();
+    });
+    return table;
+}
+
+int ilog2(int64_t n) {
+    int l = 0;
+    while ((int64_t(1) << l) < n) ++l;
+    return l;
+}
+
+constexpr uint32_t kKnownFlags = FFT_FLAG_UNNORMALIZED | FFT_FLAG_SCALE_FORWARD;
+
+}  // namespace
+
+struct gbfft_plan {
+    int64_t n = 0, batch = 0;
+    int log2n = 0, direction = 0, dtype = 0;
+    uint32_t flags = 0;
+    int device = -1;
+    int sm_count = 0;
+    const KernelEntry* entry = nullptr;
+    const void* kernel = nullptr;
+    float* d_twiddles = nullptr;  // interleaved complex64
+    int* d_error = nullptr;
+    int64_t grid = 0;
+    float scale = 1.0f;
+};
+
+extern "C" {
+
+const char* fft_version(void) { return "0.1.0"; }
+
+const char* fft_status_string(fft_status_t s) {
+    switch (s) {
+        case FFT_OK: return "success";
+        case FFT_ERR_INVALID_SIZE: return "transform length must be a power of two in [2, 2048]";
+        case FFT_ERR_INVALID_VALUE: return "invalid argument";
+        case FFT_ERR_MISALIGNED: return "input and output must be 16-byte aligned";
+        case FFT_ERR_OVERLAP: return "input and output overlap without being the same buffer";
+        case FFT_ERR_ALLOC: return "allocation failed";
+        case FFT_ERR_CUDA: return "CUDA runtime error";
+        case FFT_ERR_UNSUPPORTED: return "unsupported by this build";
+        case FFT_ERR_TIMEOUT: return "device-side wait timed out";
+        case FFT_ERR_DEVICE_CHECK: return "device-side check failed";
+        case FFT_ERR_NO_DEVICE: return "no usable CUDA device (sm_103 required)";
+    }
+    return "unknown status";
+}
+
+void fft_twiddle_fp32(int64_t m, int64_t k, float* out) {
+    // omega_m^k = exp(-2 pi i k / m).  Reduce k to [0, m), split the angle
+    // into a quadrant q (a factor (-i)^q, exact) and alpha in [0, pi/2),
+    // folded to [0, pi/4] so libm sees small arguments.
+    if (m <= 0) {
+        out[0] = 1.0f;
+        out[1] = 0.0f;
+        return;
+    }
+    k %= m;
+    if (k < 0) k += m;
+    const int64_t q = (4 * k) / m;      // quadrant 0..3
+    const int64_t r = 4 * k - q * m;    // alpha = (pi/2) * r / m, r in [0, m)
+    const double half_pi = 1.57079632679489661923;
+    double c, s;
+    if (2 * r <= m) {
+        const double a = half_pi * (double)r / (double)m;
+        c = cos(a);
+        s = sin(a);
+    } else {
+        const double b = half_pi * (double)(m - r) / (double)m;  // pi/2 - alpha
+        c = sin(b);
+        s = cos(b);
+    }
+    // e^{-i alpha} = (c, -s); times (-i)^q
+    double re, im;
+    switch (q) {
+        case 0: re = c; im = -s; break;
+        case 1: re = -s; im = -c; break;
+        case 2: re = -c; im = s; break;
+        default: re = s; im = c; break;
+    }
+    out[0] = (float)re;
+    out[1] = (float)im;
+}
+
+fft_status_t fft_validate(int64_t n, int64_t batch, int direction, int dtype, uint32_t flags) {
+    if (n < 2 || n > 2048 || (n & (n - 1)) != 0) return FFT_ERR_INVALID_SIZE;
+    if (batch < 0) return FFT_ERR_INVALID_VALUE;
+    if (batch > INT64_MAX / (16 * n)) return FFT_ERR_INVALID_VALUE;  // byte count must fit
+    if (direction != FFT_FORWARD && direction != FFT_INVERSE) return FFT_ERR_INVALID_VALUE;
+    if (dtype != FFT_C64 && dtype != FFT_C64_TC_F16 && dtype != FFT_C64_TC_BF16) return FFT_ERR_INVALID_VALUE;
+    if (flags & ~kKnownFlags) return FFT_ERR_INVALID_VALUE;
+    if (dtype != FFT_C64) return FFT_ERR_UNSUPPORTED;
+    return FFT_OK;
+}
+
+fft_status_t fft_plan_create_ex(int64_t n, int64_t batch, int direction, int dtype, uint32_t flags,
+                                fft_plan_t* plan) {
+    if (!plan) return FFT_ERR_INVALID_VALUE;
+    fft_status_t st = fft_validate(n, batch, direction, dtype, flags);
+    if (st != FFT_OK) return st;
+
+    int count = 0;
+    if (cudaGetDeviceCount(&count) != cudaSuccess || count == 0) {
+        cudaGetLastError();
+        return FFT_ERR_NO_DEVICE;
+    }
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return FFT_ERR_NO_DEVICE;
+    int major = 0, minor = 0, sms = 0;
+    if (cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return FFT_ERR_CUDA;
+    if (major != 10 || minor != 3) return FFT_ERR_NO_DEVICE;
+
+    const int log2n = ilog2(n);
+    const KernelEntry* e = &registry()[log2n];
+    gbfft_plan* p = new (std::nothrow) gbfft_plan();
+    if (!p) return FFT_ERR_ALLOC;
+    p->n = n;
+    p->batch = batch;
+    p->log2n = log2n;
+    p->direction = direction;
+    p->dtype = dtype;
+    p->flags = flags;
+    p->device = dev;
+    p->sm_count = sms;
+    p->entry = e;
+    p->kernel = direction == FFT_INVERSE ? e->kernel_inv : e->kernel_fwd;
+    const bool scaled = direction == FFT_INVERSE ? !(flags & FFT_FLAG_UNNORMALIZED)
+                                                 : (flags & FFT_FLAG_SCALE_FORWARD) != 0;
+    p->scale = scaled ? 1.0f / (float)n : 1.0f;  // a power of two: exact
+
+    // twiddle table (+ error word) in one allocation
+    const size_t tw_bytes = (size_t)e->twiddles * 2 * sizeof(float);
+    const size_t alloc = tw_bytes + 256;
+    void* dmem = nullptr;
+    if (cudaMalloc(&dmem, alloc) != cudaSuccess) {
+        cudaGetLastError();
+        delete p;
+        return FFT_ERR_ALLOC;
+    }
+    p->d_twiddles = (float*)dmem;
+    p->d_error = (int*)((char*)dmem + tw_bytes);
+    if (e->twiddles > 0) {
+        float* host = (float*)malloc(tw_bytes);
+        if (!host) {
+            cudaFree(dmem);
+            delete p;
+            return FFT_ERR_ALLOC;
+        }
+        e->fill_twiddles(host);
+        cudaError_t ce = cudaMemcpy(p->d_twiddles, host, tw_bytes, cudaMemcpyHostToDevice);
+        free(host);
+        if (ce != cudaSuccess) {
+            cudaFree(dmem);
+            delete p;
+            return FFT_ERR_CUDA;
+        }
+    }
+    if (cudaMemset(p->d_error, 0, sizeof(int)) != cudaSuccess) {
+        cudaFree(dmem);
+        delete p;
+        return FFT_ERR_CUDA;
+    }
+
+    // launch shape: persistent grid, enough resident blocks to fill every SM
+    if (e->smem_bytes > 48 * 1024) {
+        if (cudaFuncSetAttribute(p->kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, e->smem_bytes) !=
+            cudaSuccess) {
+            cudaFree(dmem);
+            delete p;
+            return FFT_ERR_CUDA;
+        }
+    }
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, p->kernel, e->threads_per_block,
+                                                      e->smem_bytes) != cudaSuccess ||
+        per_sm < 1) {
+        cudaGetLastError();
+        cudaFree(dmem);
+        delete p;
+        return FFT_ERR_CUDA;
+    }
+    int64_t tiles;
+    if (e->small) {
+        const int64_t warp_tiles = (batch + 31) / 32;
+        const int64_t warps = e->threads_per_block / 32;
+        tiles = (warp_tiles + warps - 1) / warps;
+    } else {
+        tiles = (batch + e->signals_per_block - 1) / e->signals_per_block;
+    }
+    const int64_t resident = (int64_t)sms * per_sm;
+    p->grid = tiles < resident ? tiles : resident;
+    *plan = p;
+    return FFT_OK;
+}
+
+fft_status_t fft_plan_create(int64_t n, int64_t batch, int direction, int dtype, fft_plan_t* plan) {
+    return fft_plan_create_ex(n, batch, direction, dtype, 0u, plan);
+}
+
+fft_status_t fft_execute(fft_plan_t p, const void* in, void* out, void* stream) {
+    if (!p) return FFT_ERR_INVALID_VALUE;
+    if (p->batch == 0) return FFT_OK;
+    if (!in || !out) return FFT_ERR_INVALID_VALUE;
+    if (((uintptr_t)in & 15) || ((uintptr_t)out & 15)) return FFT_ERR_MISALIGNED;
+    const uintptr_t bytes = (uintptr_t)(p->n * p->batch * 8);
+    const uintptr_t a = (uintptr_t)in, b = (uintptr_t)out;
+    if (a != b && a < b + bytes && b < a + bytes) return FFT_ERR_OVERLAP;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != p->device) return FFT_ERR_INVALID_VALUE;
+
+    const KernelEntry* e = p->entry;
+    const float2* in2 = (const float2*)in;
+    float2* out2 = (float2*)out;
+    int64_t batch = p->batch;
+    const float2* tw = (const float2*)p->d_twiddles;
+    float scale = p->scale;
+    cudaError_t ce;
+    if (e->small) {
+        void* args[] = {&in2, &out2, &batch, &scale};
+        ce = cudaLaunchKernel(p->kernel, dim3((unsigned)p->grid), dim3(e->threads_per_block), args,
+                              (size_t)e->smem_bytes, (cudaStream_t)stream);
+    } else {
+        void* args[] = {&in2, &out2, &batch, &tw, &scale};
+        ce = cudaLaunchKernel(p->kernel, dim3((unsigned)p->grid), dim3(e->threads_per_block), args,
+                              (size_t)e->smem_bytes, (cudaStream_t)stream);
+    }
+    if (ce != cudaSuccess) {
+        cudaGetLastError();
+        return FFT_ERR_CUDA;
+    }
+    return FFT_OK;
+}
+
+fft_status_t fft_plan_get_error(fft_plan_t p) {
+    if (!p) return FFT_ERR_INVALID_VALUE;
+    int word = 0;
+    if (cudaMemcpy(&word, p->d_error, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return FFT_ERR_CUDA;
+    if (word != 0) {
+        const int zero = 0;
+        if (cudaMemcpy(p->d_error, &zero, sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess) return FFT_ERR_CUDA;
+    }
+    return (fft_status_t)word;
+}
+
+fft_status_t fft_plan_destroy(fft_plan_t p) {
+    if (!p) return FFT_OK;
+    fft_status_t st = FFT_OK;
+    if (p->d_twiddles && cudaFree(p->d_twiddles) != cudaSuccess) st = FFT_ERR_CUDA;
+    delete p;
+    return st;
+}
+
+fft_status_t fft_plan_get_info(fft_plan_t p, fft_plan_info_t* info) {
+    if (!p || !info) return FFT_ERR_INVALID_VALUE;
+    memset(info, 0, sizeof(*info));
+    const KernelEntry* e = p->entry;
+    info->n = p->n;
+    info->batch = p->batch;
+    info->direction = p->direction;
+    info->dtype = p->dtype;
+    info->flags = p->flags;
+    info->elems_per_thread = e->elems_per_thread;
+    info->signals_per_block = e->signals_per_block;
+    info->threads_per_block = e->threads_per_block;
+    info->num_stages = e->num_stages;
+    for (int s = 0; s < e->num_stages && s < 4; ++s) info->radix[s] = e->radix[s];
+    info->grid = p->grid;
+    info->smem_bytes = e->smem_bytes;
+    info->twiddle_count = e->twiddles;
+    return FFT_OK;
+}
+
+fft_status_t fft_plan_get_twiddles(fft_plan_t p, void* host_out, int64_t count) {
+    if (!p || (!host_out && count > 0)) return FFT_ERR_INVALID_VALUE;
+    if (count != p->entry->twiddles) return FFT_ERR_INVALID_VALUE;
+    if (count == 0) return FFT_OK;
+    if (cudaMemcpy(host_out, p->d_twiddles, (size_t)count * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return FFT_ERR_CUDA;
+    return FFT_OK;
+}
+
+}  // extern "C"

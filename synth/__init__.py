@@ -11,7 +11,7 @@ signal-contiguous (batch stride n), the layout the library consumes.
 Workloads (each one is what the paper or the benchmark definition describes):
   * ``uniform``   - re/im iid U[-1, 1]                       (batched sweeps)
   * ``normal``    - re/im iid N(0, 1)                        (gradient loss)
-  * ``ramp``      - x_n = n, the paper's test input f(x) = x (Sec. 5)
+  * ``ramp``      - x_n = n, the paper's test input f(x) = x (Sec. 6)
   * ``ragged_lengths`` - log2 N uniform over {lo..hi}        (mixed lengths)
   * ``scaled_normal``  - N(0,1) signals scaled by 10^U(-3,3) per signal
 """

@@ -2,7 +2,7 @@
 
 Each ``pin_*`` takes an ``oracle.Oracle`` and raises AssertionError when the
 oracle disagrees with something other than itself: hand-evaluated values,
-closed forms, theorems of the DFT, the identities of Sec. 2 rebuilt from
+closed forms, theorems of the DFT, the identities of Sec. 3.1 rebuilt from
 smaller transforms, an independent library FFT (numpy's pocketfft, used only
 here) and finite differences.  The set is chosen so that every planted
 mistake in ``oracle.MUTANTS`` fails at least one pin (checked by a test).
@@ -95,7 +95,7 @@ def pin_single_tone(orc):
 def ramp_closed_form(n, inverse=False):
     """DFT of x_k = k (the paper's f(x) = x): X_0 = N(N-1)/2 and, for k != 0,
     X_k = N/(omega^k - 1) = -N/2 + i (N/2) cot(pi k / N).  The inverse
-    (Eq. (2), with 1/N) is the conjugate divided by N."""
+    (Eq. (idft), with 1/N) is the conjugate divided by N."""
     k = np.arange(n)
     out = np.empty(n, np.complex128)
     out[0] = n * (n - 1) / 2.0
@@ -209,7 +209,7 @@ def pin_conjugate_symmetry(orc):
 
 
 def pin_radix2_identity(orc):
-    """Eq. (3)/(4) rebuilt from two half-length DFTs of the naive routine."""
+    """Eq. (radix2) rebuilt from two half-length DFTs of the naive routine."""
     rng = _rng(18)
     for n in [4, 8, 16, 32, 64, 128, 256]:
         x = _crandn(rng, n)
@@ -222,7 +222,7 @@ def pin_radix2_identity(orc):
 
 
 def pin_split_radix_identity(orc):
-    """Sec. 2 split-radix: X_k = E_k + w^k O_k + w^{3k} O'_k and its three
+    """Sec. 3.1 split-radix, Eq. (split-radix-final): X_k = E_k + w^k O_k + w^{3k} O'_k and its three
     companions at k + N/4, k + N/2, k + 3N/4 (k < N/4), E the N/2-point DFT
     of the even samples, O / O' the N/4-point DFTs of samples 4n+1 / 4n+3."""
     rng = _rng(19)
