@@ -219,6 +219,11 @@ def run_ours(args):
     stream = torch.cuda.current_stream(dev)
 
     # plans and resident inputs (not timed)
+    global ELEMS, LOG2NS
+    if args.elems:
+        ELEMS = int(args.elems)
+    if args.only_n:
+        LOG2NS = [int(math.log2(int(v))) for v in args.only_n.split(",")]
     x = synth.uniform(1, ELEMS, seed=1 + rank, device=dev).reshape(-1)
     out = torch.empty_like(x)
     plans = {k: gb.Plan(2 ** k, ELEMS // 2 ** k, device=dev) for k in LOG2NS}
@@ -267,7 +272,7 @@ def run_ours(args):
 
     # end-to-end through the C-ABI with pinned host buffers, one length per call
     e2e = None
-    if rank == 0 or world > 1:
+    if not args.no_e2e:
         hx = torch.empty(ELEMS, dtype=torch.complex64, pin_memory=True)
         hx.copy_(x)
         hy = torch.empty_like(hx, pin_memory=True)
@@ -346,6 +351,9 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
+    ap.add_argument("--only-n", default="", help="comma list of lengths (profiling runs)")
+    ap.add_argument("--elems", type=int, default=0, help="elements per length (profiling runs)")
     args = ap.parse_args(argv)
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

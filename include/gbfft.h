@@ -60,8 +60,12 @@ enum {
     FFT_FLAG_UNNORMALIZED = 1u << 0,
     /* With FFT_FORWARD: multiply by 1/N, giving (1/N) F, the adjoint of the
      * normalised inverse (used for the backward pass of an inverse). */
-    FFT_FLAG_SCALE_FORWARD = 1u << 1
+    FFT_FLAG_SCALE_FORWARD = 1u << 1,
+    /* Bits 8..11: 1 + the schedule variant to use (0 = the length's default,
+     * see fft_set_default_variant).  Build them with FFT_FLAG_VARIANT(k). */
+    FFT_FLAG_VARIANT_MASK = 0xFu << 8
 };
+#define FFT_FLAG_VARIANT(k) ((uint32_t)((k) + 1) << 8)
 
 typedef enum {
     FFT_OK = 0,
@@ -131,12 +135,36 @@ typedef struct {
     int threads_per_block;
     int num_stages;         /* radix stages, first to last                      */
     int radix[8];
+    int variant;            /* schedule variant of this length in use           */
+    int pipeline;           /* bulk-copy (TMA) prefetch ring depth, 0 = none     */
+    int min_blocks;         /* launch-bounds residency hint                     */
+    int kernel_kind;        /* 0 one thread per signal, 1 direct, 2 TMA ring    */
     int64_t grid;           /* blocks launched (persistent grid-stride loop)    */
     int64_t smem_bytes;     /* dynamic shared memory per block                  */
     int64_t twiddle_count;  /* complex64 entries in the plan's twiddle table    */
 } fft_plan_info_t;
 
 GBFFT_API fft_status_t fft_plan_get_info(fft_plan_t plan, fft_plan_info_t* info);
+
+/*
+ * Schedule variants.  Each length has one or more compiled radix schedules /
+ * launch shapes (the analogue of the paper's host-chosen stage_sizes and
+ * work-group factor, Sec. 4).  fft_variant_count returns how many (0 for an
+ * invalid length); fft_set_default_variant chooses the one later plans of
+ * that length use (process-wide; the autotuner calls it); plans already made
+ * keep theirs.  fft_get_default_variant returns the current choice or -1.
+ */
+GBFFT_API int fft_variant_count(int64_t n);
+GBFFT_API fft_status_t fft_set_default_variant(int64_t n, int variant);
+GBFFT_API int fft_get_default_variant(int64_t n);
+
+/*
+ * Wall-time limit for the device-side waits of this plan's kernels (the
+ * bulk-copy prefetch ring waits on mbarriers).  A wait that runs out records
+ * FFT_ERR_TIMEOUT in the plan's error word (see fft_plan_get_error), stops
+ * waiting and lets the kernel finish.  Default 4 s.  0 is rejected.
+ */
+GBFFT_API fft_status_t fft_plan_set_wait_limit(fft_plan_t plan, uint64_t nanoseconds);
 
 /*
  * Copy the plan's FP32 twiddle table (twiddle_count complex64 entries) into

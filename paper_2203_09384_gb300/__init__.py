@@ -17,7 +17,8 @@ import threading
 import torch
 
 from ._abi import (FFT_C64, FFT_C64_TC_BF16, FFT_C64_TC_F16, FFT_FLAG_SCALE_FORWARD,  # noqa: F401
-                   FFT_FLAG_UNNORMALIZED,
+                   FFT_FLAG_UNNORMALIZED, FFT_FLAG_VARIANT, fft_get_default_variant,
+                   fft_set_default_variant, fft_variant_count,
                    FFT_FORWARD, FFT_INVERSE, FFTError, STATUS, fft_execute, fft_plan_create,
                    fft_plan_create_ex, fft_plan_destroy, fft_plan_get_error, fft_plan_get_info,
                    fft_validate, lib)
@@ -37,7 +38,8 @@ class Plan:
     """
 
     def __init__(self, n: int, batch: int, inverse: bool = False, dtype: str = "c64",
-                 normalized: bool = True, device=None, scale_forward: bool = False):
+                 normalized: bool = True, device=None, scale_forward: bool = False,
+                 variant: int | None = None):
         self.n, self.batch, self.inverse = int(n), int(batch), bool(inverse)
         self.dtype = dtype
         self.normalized = normalized
@@ -46,6 +48,8 @@ class Plan:
         flags = 0 if normalized else FFT_FLAG_UNNORMALIZED
         if scale_forward and not inverse:
             flags |= FFT_FLAG_SCALE_FORWARD
+        if variant is not None:
+            flags |= FFT_FLAG_VARIANT(variant)
         direction = FFT_INVERSE if inverse else FFT_FORWARD
         self.handle = None
         with torch.cuda.device(self.device):

@@ -20,6 +20,11 @@ FFT_C64_TC_F16 = 1
 FFT_C64_TC_BF16 = 2
 FFT_FLAG_UNNORMALIZED = 1 << 0
 FFT_FLAG_SCALE_FORWARD = 1 << 1
+FFT_FLAG_VARIANT_MASK = 0xF << 8
+
+
+def FFT_FLAG_VARIANT(k: int) -> int:
+    return (k + 1) << 8
 
 STATUS = {
     0: "FFT_OK",
@@ -61,6 +66,10 @@ class PlanInfo(ctypes.Structure):
         ("threads_per_block", ctypes.c_int),
         ("num_stages", ctypes.c_int),
         ("radix", ctypes.c_int * 8),
+        ("variant", ctypes.c_int),
+        ("pipeline", ctypes.c_int),
+        ("min_blocks", ctypes.c_int),
+        ("kernel_kind", ctypes.c_int),
         ("grid", ctypes.c_int64),
         ("smem_bytes", ctypes.c_int64),
         ("twiddle_count", ctypes.c_int64),
@@ -111,6 +120,14 @@ def lib() -> ctypes.CDLL:
     L.fft_plan_get_info.argtypes = [_vp, ctypes.POINTER(PlanInfo)]
     L.fft_plan_get_twiddles.restype = _int
     L.fft_plan_get_twiddles.argtypes = [_vp, _vp, _i64]
+    L.fft_variant_count.restype = _int
+    L.fft_variant_count.argtypes = [_i64]
+    L.fft_set_default_variant.restype = _int
+    L.fft_set_default_variant.argtypes = [_i64, _int]
+    L.fft_get_default_variant.restype = _int
+    L.fft_get_default_variant.argtypes = [_i64]
+    L.fft_plan_set_wait_limit.restype = _int
+    L.fft_plan_set_wait_limit.argtypes = [_vp, ctypes.c_uint64]
     L.fft_twiddle_fp32.restype = None
     L.fft_twiddle_fp32.argtypes = [_i64, _i64, ctypes.POINTER(ctypes.c_float)]
     _lib = L
@@ -163,3 +180,19 @@ def fft_twiddle_fp32(m: int, k: int) -> complex:
     out = (ctypes.c_float * 2)()
     lib().fft_twiddle_fp32(m, k, out)
     return complex(out[0], out[1])
+
+
+def fft_variant_count(n: int) -> int:
+    return lib().fft_variant_count(n)
+
+
+def fft_set_default_variant(n: int, variant: int) -> None:
+    check(lib().fft_set_default_variant(n, variant), "fft_set_default_variant")
+
+
+def fft_get_default_variant(n: int) -> int:
+    return lib().fft_get_default_variant(n)
+
+
+def fft_plan_set_wait_limit(plan: int, nanoseconds: int) -> None:
+    check(lib().fft_plan_set_wait_limit(plan, nanoseconds), "fft_plan_set_wait_limit")

@@ -139,6 +139,47 @@ struct Dft<16> {
     }
 };
 
+// cos and sin of pi/16 and 3 pi/16 for the radix-32 butterfly
+constexpr float kCos16 = 0.98078528040323044913f;
+constexpr float kSin16 = 0.19509032201612826785f;
+constexpr float kCos316 = 0.83146961230254523708f;
+constexpr float kSin316 = 0.55557023301960222474f;
+
+template <>
+struct Dft<32> {
+    // radix-2 split (Eq. (radix2)) over two 16-point DFTs; omega_32^k, k < 16
+    static __device__ __forceinline__ void run(float2* v) {
+        float2 e[16], o[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            e[i] = v[2 * i];
+            o[i] = v[2 * i + 1];
+        }
+        Dft<16>::run(e);
+        Dft<16>::run(o);
+        o[1] = cmul(o[1], make_float2(kCos16, -kSin16));
+        o[2] = cmul(o[2], make_float2(kCos8, -kSin8));
+        o[3] = cmul(o[3], make_float2(kCos316, -kSin316));
+        o[4] = mul_w8_1(o[4]);
+        o[5] = cmul(o[5], make_float2(kSin316, -kCos316));
+        o[6] = cmul(o[6], make_float2(kSin8, -kCos8));
+        o[7] = cmul(o[7], make_float2(kSin16, -kCos16));
+        o[8] = mul_neg_i(o[8]);
+        o[9] = cmul(o[9], make_float2(-kSin16, -kCos16));
+        o[10] = cmul(o[10], make_float2(-kSin8, -kCos8));
+        o[11] = cmul(o[11], make_float2(-kSin316, -kCos316));
+        o[12] = mul_w8_3(o[12]);
+        o[13] = cmul(o[13], make_float2(-kCos316, -kSin316));
+        o[14] = cmul(o[14], make_float2(-kCos8, -kSin8));
+        o[15] = cmul(o[15], make_float2(-kCos16, -kSin16));
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            v[k] = cadd(e[k], o[k]);
+            v[k + 16] = csub(e[k], o[k]);
+        }
+    }
+};
+
 // ---------------------------------------------------------------------------
 // memory helpers: streaming (evict-first) 64/128-bit global accesses
 // ---------------------------------------------------------------------------
@@ -157,9 +198,71 @@ __device__ __forceinline__ int swz8(int a) { return a ^ ((a >> 4) & 15); }
 __device__ __forceinline__ int swz16(int a) { return a ^ ((a >> 3) & 7); }
 
 // ---------------------------------------------------------------------------
+// Bulk copy (TMA, non-tensor form) and mbarrier primitives, inline PTX
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// order this thread's earlier generic-proxy shared accesses before later
+// async-proxy (bulk copy) accesses
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+// global -> shared bulk copy; completion is signalled on `bar` as tx bytes.
+// dst, src 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ uint64_t global_timer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Wait for phase `parity` of `bar` to complete, giving up after limit_ns of
+// wall time.  Returns false on timeout (the caller records the error).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint64_t limit_ns) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_timer_ns();
+    for (;;) {
+#pragma unroll 1
+        for (int i = 0; i < 32; ++i)
+            if (mbar_try_wait(bar, parity)) return true;
+        if (global_timer_ns() - t0 > limit_ns) return false;
+    }
+}
+
+// status code written to the plan's error word by a wait that gave up
+constexpr int kErrTimeout = 8;
+
+// ---------------------------------------------------------------------------
 // Compile-time schedule
 // ---------------------------------------------------------------------------
-template <int LOG2N_, int E_, int S_, int R0, int R1, int R2, int R3>
+template <int LOG2N_, int E_, int S_, int R0, int R1, int R2, int R3, int MINB_ = 1, int PIPE_ = 0>
 struct Cfg {
     static constexpr int LOG2N = LOG2N_;
     static constexpr int N = 1 << LOG2N_;
@@ -167,10 +270,14 @@ struct Cfg {
     static constexpr int S = S_;          // signals per tile (per block)
     static constexpr int T = N / E;       // threads per signal
     static constexpr int NT = T * S;      // threads per block
+    static constexpr int MINB = MINB_;    // min resident blocks per SM (launch bounds)
+    static constexpr int PIPE = PIPE_;    // 0: direct loads; D: bulk-copy ring of D tiles
     static constexpr int M = (R0 > 0) + (R1 > 0) + (R2 > 0) + (R3 > 0);
     static constexpr bool kWarpLocal = T <= 32;  // a signal never spans warps
     static constexpr int kBuffers = kWarpLocal ? 1 : 2;
-    static constexpr int kSmemElems = kBuffers * S * N;
+    static constexpr int kSmemElems = kBuffers * S * N;           // exchange buffers
+    static constexpr int kRingElems = PIPE * S * N;               // prefetch ring
+    static constexpr int kSmemBytes = (kSmemElems + kRingElems) * 8 + (PIPE > 0 ? 8 * PIPE : 0);
     __host__ __device__ static constexpr int radix(int s) {
         return s == 0 ? R0 : s == 1 ? R1 : s == 2 ? R2 : R3;
     }
@@ -194,6 +301,8 @@ struct Cfg {
                       (R3 == 0 || E % R3 == 0),
                   "every radix must divide E");
     static_assert(32 % T == 0 || T % 32 == 0, "T must tile warps");
+    static_assert(PIPE == 0 || (PIPE >= 2 && !kWarpLocal),
+                  "the bulk-copy ring needs block-wide exchanges (T > 32)");
 };
 
 // Butterfly handled by thread t in slot c of stage s.  The first and the last
@@ -202,7 +311,8 @@ struct Cfg {
 template <class C, int s>
 __device__ __forceinline__ int bfly(int t, int c) {
     constexpr int K = C::E / C::radix(s);
-    if constexpr (s == 0 || s == C::M - 1) {
+    // with the bulk-copy ring, stage 0 reads shared memory: interleave threads
+    if constexpr ((s == 0 && C::PIPE == 0) || s == C::M - 1) {
         return K * t + c;
     } else {
         return t + C::T * c;
@@ -334,8 +444,11 @@ __device__ __forceinline__ void rest_stages(float2 (&v)[C::E], float2* smem, int
 
 // The generic kernel: N = 32..2048.
 template <class C, bool INV>
-__global__ void __launch_bounds__(C::NT) fft_stockham_kernel(const float2* in, float2* out, int64_t batch,
-                                                             const float2* __restrict__ tw, float scale) {
+__global__ void __launch_bounds__(C::NT, C::MINB)
+    fft_stockham_kernel(const float2* in, float2* out, int64_t batch, const float2* __restrict__ tw, float scale,
+                        int* err, uint64_t wait_ns) {
+    (void)err;
+    (void)wait_ns;
     extern __shared__ __align__(16) float2 smem[];
     const int tid = threadIdx.x;
     const int sl = tid / C::T;
@@ -355,31 +468,118 @@ __global__ void __launch_bounds__(C::NT) fft_stockham_kernel(const float2* in, f
     }
 }
 
+// stage-0 inputs from a dense tile in shared memory (the bulk-copy ring)
+template <class C, bool INV>
+__device__ __forceinline__ void gather_tile(float2 (&v)[C::E], const float2* tile, int sb, int t) {
+    constexpr int R = C::radix(0);
+    constexpr int K = C::E / R;
+    constexpr int stride = C::N / R;
+#pragma unroll
+    for (int c = 0; c < K; ++c) {
+        const int j = bfly<C, 0>(t, c);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            float2 a = tile[sb + j + r * stride];
+            v[c * R + r] = INV ? conj2(a) : a;
+        }
+    }
+}
+
+// The generic kernel with a bulk-copy (TMA) prefetch ring: thread 0 keeps
+// PIPE tiles in flight from HBM into shared memory, each completion tracked by
+// an mbarrier's transaction count, so HBM latency is hidden by copies in
+// flight rather than by registers.  A ring slot is refilled as soon as the
+// first exchange barrier shows every thread has read it.  Waits are bounded:
+// on timeout the kernel records FFT_ERR_TIMEOUT, stops waiting and finishes.
+template <class C, bool INV>
+__global__ void __launch_bounds__(C::NT, C::MINB)
+    fft_stockham_ring_kernel(const float2* in, float2* out, int64_t batch, const float2* __restrict__ tw,
+                             float scale, int* err, uint64_t wait_ns) {
+    constexpr int D = C::PIPE;
+    constexpr int TILE = C::S * C::N;
+    extern __shared__ __align__(128) float2 smem[];
+    float2* ring = smem + C::kSmemElems;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(ring + D * TILE);
+    const int tid = threadIdx.x;
+    const int sl = tid / C::T;
+    const int t = tid % C::T;
+    const int sb = sl * C::N;
+    const int64_t ntiles = (batch + C::S - 1) / C::S;
+
+    auto issue = [&](int slot, int64_t tile) {  // thread 0 only
+        const int64_t first = tile * C::S;
+        const int64_t left = batch - first;
+        const uint32_t bytes = (uint32_t)((left < C::S ? left : C::S) * C::N * 8);
+        mbar_arrive_expect_tx(&bars[slot], bytes);
+        bulk_copy_g2s(ring + slot * TILE, in + first * C::N, bytes, &bars[slot]);
+    };
+    if (tid == 0) {
+        for (int d = 0; d < D; ++d) mbar_init(&bars[d], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (tid == 0) {
+        for (int d = 0; d < D; ++d) {
+            const int64_t tile = blockIdx.x + (int64_t)d * gridDim.x;
+            if (tile < ntiles) issue(d, tile);
+        }
+    }
+    bool dead = false;
+    int buf = 0;
+    int64_t it = 0;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+        const int slot = (int)(it % D);
+        const uint32_t parity = (uint32_t)((it / D) & 1);
+        if (!dead && !mbar_wait_bounded(&bars[slot], parity, wait_ns)) {
+            dead = true;
+            atomicCAS(err, 0, kErrTimeout);
+        }
+        const int64_t sig = tile * C::S + sl;
+        const bool active = sig < batch && !dead;
+        float2 v[C::E];
+        gather_tile<C, INV>(v, ring + slot * TILE, sb, t);
+        twist_and_dft<C, 0>(v, t, tw);
+        float2* b = smem + buf * TILE;
+        scatter<C, 0>(v, b, sb, t);
+        __syncthreads();  // every thread is done with ring[slot]
+        if (tid == 0 && !dead) {
+            const int64_t next = tile + (int64_t)D * gridDim.x;
+            if (next < ntiles) {
+                fence_proxy_async_smem();
+                issue(slot, next);
+            }
+        }
+        gather<C, 1>(v, b, sb, t);
+        buf ^= 1;
+        twist_and_dft<C, 1>(v, t, tw);
+        rest_stages<C, 2>(v, smem, buf, sb, t, tw);
+        store_last<C, INV>(v, out + sig * C::N, t, active, scale);
+    }
+}
+
 // ---------------------------------------------------------------------------
-// N = 2..16: one thread owns a whole signal.  Each warp stages a contiguous
+// N = 2..32: one thread owns a whole signal.  Each warp stages a contiguous
 // tile of 32 signals through shared memory with coalesced 128-bit copies, so
 // HBM sees fully used sectors while each thread reads its own signal.
 // ---------------------------------------------------------------------------
-constexpr int kSmallWarps = 8;
-
-template <int LOG2N>
+template <int LOG2N, int WARPS>
 struct SmallCfg {
     static constexpr int N = 1 << LOG2N;
     static constexpr int H = N / 2;  // float4 slots per signal
-    static constexpr int NT = 32 * kSmallWarps;
-    static constexpr int kSmemBytes = kSmallWarps * 32 * H * 16;
+    static constexpr int WARPS_PER_BLOCK = WARPS;
+    static constexpr int NT = 32 * WARPS;
+    static constexpr int kSmemBytes = WARPS * 32 * H * 16;
 };
 
-template <int LOG2N, bool INV>
-__global__ void __launch_bounds__(SmallCfg<LOG2N>::NT) fft_small_kernel(const float2* in, float2* out, int64_t batch,
-                                                                        float scale) {
-    using C = SmallCfg<LOG2N>;
-    constexpr int N = C::N, H = C::H;
+template <class SC, bool INV>
+__global__ void __launch_bounds__(SC::NT) fft_small_kernel(const float2* in, float2* out, int64_t batch,
+                                                           float scale) {
+    constexpr int N = SC::N, H = SC::H, W = SC::WARPS_PER_BLOCK;
     extern __shared__ __align__(16) float4 smem4[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float4* sm = smem4 + warp * (32 * H);
     const int64_t wtiles = (batch + 31) / 32;
-    for (int64_t wt = (int64_t)blockIdx.x * kSmallWarps + warp; wt < wtiles; wt += (int64_t)gridDim.x * kSmallWarps) {
+    for (int64_t wt = (int64_t)blockIdx.x * W + warp; wt < wtiles; wt += (int64_t)gridDim.x * W) {
         const int64_t first = wt * 32;
         const int64_t left = batch - first;
         const int valid4 = (int)((left < 32 ? left : 32) * H);

@@ -12,27 +12,6 @@
 
 namespace gbfft {
 
-template <int L>
-struct Sched;
-
-#define GBFFT_GENERIC_SCHED(L, E, S, R0, R1, R2, R3)  \
-    template <>                                       \
-    struct Sched<L> {                                 \
-        using type = Cfg<L, E, S, R0, R1, R2, R3>;    \
-        static constexpr bool small = false;          \
-    };
-GBFFT_SCHEDULES(GBFFT_GENERIC_SCHED)
-#undef GBFFT_GENERIC_SCHED
-
-#define GBFFT_SMALL_SCHED(L)                   \
-    template <>                                \
-    struct Sched<L> {                          \
-        using type = SmallCfg<L>;              \
-        static constexpr bool small = true;    \
-    };
-GBFFT_SMALL_SCHEDULES(GBFFT_SMALL_SCHED)
-#undef GBFFT_SMALL_SCHED
-
 // Twiddle table of a generic schedule: for each stage s >= 1 with radix R and
 // Ns = R_0 * ... * R_{s-1}, entry tw_off(s) + (r - 1) * Ns + m holds
 // omega_{Ns*R}^{m*r} for r = 1..R-1, m = 0..Ns-1 (laid out so that threads
@@ -51,44 +30,132 @@ static void fill_generic_twiddles(float* host) {
 
 static void fill_nothing(float*) {}
 
-template <int L>
-static KernelEntry make_entry() {
-    using SC = Sched<L>;
-    using C = typename SC::type;
+template <class C>
+static KernelEntry generic_entry(int variant) {
     KernelEntry e{};
-    e.log2n = L;
-    e.small = SC::small;
-    if constexpr (SC::small) {
-        e.elems_per_thread = C::N;
-        e.signals_per_block = 32 * kSmallWarps;
-        e.threads_per_block = C::NT;
-        e.smem_bytes = C::kSmemBytes;
-        e.num_stages = 1;
-        e.radix[0] = C::N;
-        e.twiddles = 0;
-        e.signals_per_warp_tile = 32;
-        e.kernel_fwd = reinterpret_cast<const void*>(&fft_small_kernel<L, false>);
-        e.kernel_inv = reinterpret_cast<const void*>(&fft_small_kernel<L, true>);
-        e.fill_twiddles = &fill_nothing;
+    e.log2n = C::LOG2N;
+    e.variant = variant;
+    e.kind = C::PIPE ? KernelKind::Ring : KernelKind::Direct;
+    e.elems_per_thread = C::E;
+    e.signals_per_block = C::S;
+    e.threads_per_block = C::NT;
+    e.smem_bytes = C::kSmemBytes;
+    e.num_stages = C::M;
+    for (int s = 0; s < 4; ++s) e.radix[s] = C::radix(s);
+    e.min_blocks = C::MINB;
+    e.pipeline = C::PIPE;
+    e.twiddles = C::kTwiddles;
+    if constexpr (C::PIPE > 0) {
+        e.kernel_fwd = reinterpret_cast<const void*>(&fft_stockham_ring_kernel<C, false>);
+        e.kernel_inv = reinterpret_cast<const void*>(&fft_stockham_ring_kernel<C, true>);
     } else {
-        e.elems_per_thread = C::E;
-        e.signals_per_block = C::S;
-        e.threads_per_block = C::NT;
-        e.smem_bytes = C::kSmemElems * (int)sizeof(float2);
-        e.num_stages = C::M;
-        for (int s = 0; s < 4; ++s) e.radix[s] = C::radix(s);
-        e.twiddles = C::kTwiddles;
-        e.signals_per_warp_tile = 0;
         e.kernel_fwd = reinterpret_cast<const void*>(&fft_stockham_kernel<C, false>);
         e.kernel_inv = reinterpret_cast<const void*>(&fft_stockham_kernel<C, true>);
-        e.fill_twiddles = &fill_generic_twiddles<C>;
     }
+    e.fill_twiddles = &fill_generic_twiddles<C>;
+    return e;
+}
+
+template <class SC>
+static KernelEntry small_entry(int variant) {
+    KernelEntry e{};
+    e.log2n = 0;
+    while ((1 << e.log2n) < SC::N) ++e.log2n;
+    e.variant = variant;
+    e.kind = KernelKind::Small;
+    e.elems_per_thread = SC::N;
+    e.signals_per_block = 32 * SC::WARPS_PER_BLOCK;
+    e.threads_per_block = SC::NT;
+    e.smem_bytes = SC::kSmemBytes;
+    e.num_stages = 1;
+    e.radix[0] = SC::N;
+    e.min_blocks = 1;
+    e.pipeline = 0;
+    e.twiddles = 0;
+    e.kernel_fwd = reinterpret_cast<const void*>(&fft_small_kernel<SC, false>);
+    e.kernel_inv = reinterpret_cast<const void*>(&fft_small_kernel<SC, true>);
+    e.fill_twiddles = &fill_nothing;
     return e;
 }
 
 }  // namespace gbfft
 
-#define GBFFT_ENTRY_FN2(L) gbfft_entry_##L
-#define GBFFT_ENTRY_FN(L) GBFFT_ENTRY_FN2(L)
+// GBFFT_ONLY_<L>(...) keeps its argument only in the build for length 2^L, so
+// each translation unit instantiates just its own length's kernels.
+#if GBFFT_LOG2N == 1
+#define GBFFT_ONLY_1(...) __VA_ARGS__
+#else
+#define GBFFT_ONLY_1(...)
+#endif
+#if GBFFT_LOG2N == 2
+#define GBFFT_ONLY_2(...) __VA_ARGS__
+#else
+#define GBFFT_ONLY_2(...)
+#endif
+#if GBFFT_LOG2N == 3
+#define GBFFT_ONLY_3(...) __VA_ARGS__
+#else
+#define GBFFT_ONLY_3(...)
+#endif
+#if GBFFT_LOG2N == 4
+#define GBFFT_ONLY_4(...) __VA_ARGS__
+#else
+#define GBFFT_ONLY_4(...)
+#endif
+#if GBFFT_LOG2N == 5
+#define GBFFT_ONLY_5(...) __VA_ARGS__
+#else
+#define GBFFT_ONLY_5(...)
+#endif
+#if GBFFT_LOG2N == 6
+#define GBFFT_ONLY_6(...) __VA_ARGS__
+#else
+#define GBFFT_ONLY_6(...)
+#endif
+#if GBFFT_LOG2N == 7
+#define GBFFT_ONLY_7(...) __VA_ARGS__
+#else
+#define GBFFT_ONLY_7(...)
+#endif
+#if GBFFT_LOG2N == 8
+#define GBFFT_ONLY_8(...) __VA_ARGS__
+#else
+#define GBFFT_ONLY_8(...)
+#endif
+#if GBFFT_LOG2N == 9
+#define GBFFT_ONLY_9(...) __VA_ARGS__
+#else
+#define GBFFT_ONLY_9(...)
+#endif
+#if GBFFT_LOG2N == 10
+#define GBFFT_ONLY_10(...) __VA_ARGS__
+#else
+#define GBFFT_ONLY_10(...)
+#endif
+#if GBFFT_LOG2N == 11
+#define GBFFT_ONLY_11(...) __VA_ARGS__
+#else
+#define GBFFT_ONLY_11(...)
+#endif
 
-gbfft::KernelEntry GBFFT_ENTRY_FN(GBFFT_LOG2N)() { return gbfft::make_entry<GBFFT_LOG2N>(); }
+#define GBFFT_ENTRIES_FN2(L) gbfft_entries_##L
+#define GBFFT_ENTRIES_FN(L) GBFFT_ENTRIES_FN2(L)
+
+int GBFFT_ENTRIES_FN(GBFFT_LOG2N)(gbfft::KernelEntry* out, int max) {
+    using namespace gbfft;
+    int count = 0;
+    auto put = [&](const KernelEntry& e) {
+        if (e.variant >= 0 && e.variant < max) {
+            out[e.variant] = e;
+            if (e.variant + 1 > count) count = e.variant + 1;
+        }
+    };
+#define GBFFT_GX(L, V, E, S, R0, R1, R2, R3, MINB, PIPE) \
+    GBFFT_ONLY_##L(put(generic_entry<Cfg<L, E, S, R0, R1, R2, R3, MINB, PIPE>>(V));)
+    GBFFT_GENERIC_SCHEDULES(GBFFT_GX)
+#undef GBFFT_GX
+#define GBFFT_SX(L, V, W) GBFFT_ONLY_##L(put(small_entry<SmallCfg<L, W>>(V));)
+    GBFFT_SMALL_SCHEDULES(GBFFT_SX)
+#undef GBFFT_SX
+    return count;
+}

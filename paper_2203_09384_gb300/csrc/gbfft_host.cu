@@ -8,6 +8,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <atomic>
 #include <mutex>
 #include <new>
 
@@ -15,37 +16,44 @@
 #include "registry.h"
 #include "schedules.h"
 
-GBFFT_DECLARE_ENTRY(1)
-GBFFT_DECLARE_ENTRY(2)
-GBFFT_DECLARE_ENTRY(3)
-GBFFT_DECLARE_ENTRY(4)
-GBFFT_DECLARE_ENTRY(5)
-GBFFT_DECLARE_ENTRY(6)
-GBFFT_DECLARE_ENTRY(7)
-GBFFT_DECLARE_ENTRY(8)
-GBFFT_DECLARE_ENTRY(9)
-GBFFT_DECLARE_ENTRY(10)
-GBFFT_DECLARE_ENTRY(11)
+GBFFT_DECLARE_ENTRIES(1)
+GBFFT_DECLARE_ENTRIES(2)
+GBFFT_DECLARE_ENTRIES(3)
+GBFFT_DECLARE_ENTRIES(4)
+GBFFT_DECLARE_ENTRIES(5)
+GBFFT_DECLARE_ENTRIES(6)
+GBFFT_DECLARE_ENTRIES(7)
+GBFFT_DECLARE_ENTRIES(8)
+GBFFT_DECLARE_ENTRIES(9)
+GBFFT_DECLARE_ENTRIES(10)
+GBFFT_DECLARE_ENTRIES(11)
 
 namespace {
 
 using gbfft::KernelEntry;
+using gbfft::KernelKind;
 
-const KernelEntry* registry() {
-    static KernelEntry table[GBFFT_MAX_LOG2N + 1];
+struct LengthVariants {
+    KernelEntry v[GBFFT_MAX_VARIANTS];
+    int count = 0;
+    std::atomic<int> preferred{0};  // variant new plans use unless told otherwise
+};
+
+LengthVariants* registry() {
+    static LengthVariants table[GBFFT_MAX_LOG2N + 1];
     static std::once_flag once;
     std::call_once(once, [] {
-        table[1] = gbfft_entry_1();
-        table[2] = gbfft_entry_2();
-        table[3] = gbfft_entry_3();
-        table[4] = gbfft_entry_4();
-        table[5] = gbfft_entry_5();
-        table[6] = gbfft_entry_6();
-        table[7] = gbfft_entry_7();
-        table[8] = gbfft_entry_8();
-        table[9] = gbfft_entry_9();
-        table[10] = gbfft_entry_10();
-        table[11] = gbfft_entry_11();
+        table[1].count = gbfft_entries_1(table[1].v, GBFFT_MAX_VARIANTS);
+        table[2].count = gbfft_entries_2(table[2].v, GBFFT_MAX_VARIANTS);
+        table[3].count = gbfft_entries_3(table[3].v, GBFFT_MAX_VARIANTS);
+        table[4].count = gbfft_entries_4(table[4].v, GBFFT_MAX_VARIANTS);
+        table[5].count = gbfft_entries_5(table[5].v, GBFFT_MAX_VARIANTS);
+        table[6].count = gbfft_entries_6(table[6].v, GBFFT_MAX_VARIANTS);
+        table[7].count = gbfft_entries_7(table[7].v, GBFFT_MAX_VARIANTS);
+        table[8].count = gbfft_entries_8(table[8].v, GBFFT_MAX_VARIANTS);
+        table[9].count = gbfft_entries_9(table[9].v, GBFFT_MAX_VARIANTS);
+        table[10].count = gbfft_entries_10(table[10].v, GBFFT_MAX_VARIANTS);
+        table[11].count = gbfft_entries_11(table[11].v, GBFFT_MAX_VARIANTS);
     });
     return table;
 }
@@ -56,7 +64,8 @@ int ilog2(int64_t n) {
     return l;
 }
 
-constexpr uint32_t kKnownFlags = FFT_FLAG_UNNORMALIZED | FFT_FLAG_SCALE_FORWARD;
+constexpr uint32_t kKnownFlags = FFT_FLAG_UNNORMALIZED | FFT_FLAG_SCALE_FORWARD | FFT_FLAG_VARIANT_MASK;
+constexpr uint64_t kDefaultWaitNs = 4000000000ull;  // bounded device waits: 4 s
 
 }  // namespace
 
@@ -72,6 +81,7 @@ struct gbfft_plan {
     int* d_error = nullptr;
     int64_t grid = 0;
     float scale = 1.0f;
+    uint64_t wait_ns = kDefaultWaitNs;
 };
 
 extern "C" {
@@ -163,7 +173,11 @@ fft_status_t fft_plan_create_ex(int64_t n, int64_t batch, int direction, int dty
     if (major != 10 || minor != 3) return FFT_ERR_NO_DEVICE;
 
     const int log2n = ilog2(n);
-    const KernelEntry* e = &registry()[log2n];
+    LengthVariants* lv = &registry()[log2n];
+    int variant = (int)((flags & FFT_FLAG_VARIANT_MASK) >> 8) - 1;
+    if (variant < 0) variant = lv->preferred.load();
+    if (variant >= lv->count || !lv->v[variant].kernel_fwd) return FFT_ERR_INVALID_VALUE;
+    const KernelEntry* e = &lv->v[variant];
     gbfft_plan* p = new (std::nothrow) gbfft_plan();
     if (!p) return FFT_ERR_ALLOC;
     p->n = n;
@@ -231,14 +245,7 @@ fft_status_t fft_plan_create_ex(int64_t n, int64_t batch, int direction, int dty
         delete p;
         return FFT_ERR_CUDA;
     }
-    int64_t tiles;
-    if (e->small) {
-        const int64_t warp_tiles = (batch + 31) / 32;
-        const int64_t warps = e->threads_per_block / 32;
-        tiles = (warp_tiles + warps - 1) / warps;
-    } else {
-        tiles = (batch + e->signals_per_block - 1) / e->signals_per_block;
-    }
+    const int64_t tiles = (batch + e->signals_per_block - 1) / e->signals_per_block;
     const int64_t resident = (int64_t)sms * per_sm;
     p->grid = tiles < resident ? tiles : resident;
     *plan = p;
@@ -266,13 +273,15 @@ fft_status_t fft_execute(fft_plan_t p, const void* in, void* out, void* stream) 
     int64_t batch = p->batch;
     const float2* tw = (const float2*)p->d_twiddles;
     float scale = p->scale;
+    int* err = p->d_error;
+    uint64_t wait_ns = p->wait_ns;
     cudaError_t ce;
-    if (e->small) {
+    if (e->kind == KernelKind::Small) {
         void* args[] = {&in2, &out2, &batch, &scale};
         ce = cudaLaunchKernel(p->kernel, dim3((unsigned)p->grid), dim3(e->threads_per_block), args,
                               (size_t)e->smem_bytes, (cudaStream_t)stream);
     } else {
-        void* args[] = {&in2, &out2, &batch, &tw, &scale};
+        void* args[] = {&in2, &out2, &batch, &tw, &scale, &err, &wait_ns};
         ce = cudaLaunchKernel(p->kernel, dim3((unsigned)p->grid), dim3(e->threads_per_block), args,
                               (size_t)e->smem_bytes, (cudaStream_t)stream);
     }
@@ -315,10 +324,38 @@ fft_status_t fft_plan_get_info(fft_plan_t p, fft_plan_info_t* info) {
     info->signals_per_block = e->signals_per_block;
     info->threads_per_block = e->threads_per_block;
     info->num_stages = e->num_stages;
+    info->variant = e->variant;
+    info->pipeline = e->pipeline;
+    info->min_blocks = e->min_blocks;
+    info->kernel_kind = (int)e->kind;
     for (int s = 0; s < e->num_stages && s < 4; ++s) info->radix[s] = e->radix[s];
     info->grid = p->grid;
     info->smem_bytes = e->smem_bytes;
     info->twiddle_count = e->twiddles;
+    return FFT_OK;
+}
+
+int fft_variant_count(int64_t n) {
+    if (n < 2 || n > 2048 || (n & (n - 1)) != 0) return 0;
+    return registry()[ilog2(n)].count;
+}
+
+fft_status_t fft_set_default_variant(int64_t n, int variant) {
+    if (n < 2 || n > 2048 || (n & (n - 1)) != 0) return FFT_ERR_INVALID_SIZE;
+    LengthVariants* lv = &registry()[ilog2(n)];
+    if (variant < 0 || variant >= lv->count || !lv->v[variant].kernel_fwd) return FFT_ERR_INVALID_VALUE;
+    lv->preferred.store(variant);
+    return FFT_OK;
+}
+
+int fft_get_default_variant(int64_t n) {
+    if (n < 2 || n > 2048 || (n & (n - 1)) != 0) return -1;
+    return registry()[ilog2(n)].preferred.load();
+}
+
+fft_status_t fft_plan_set_wait_limit(fft_plan_t p, uint64_t nanoseconds) {
+    if (!p || nanoseconds == 0) return FFT_ERR_INVALID_VALUE;
+    p->wait_ns = nanoseconds;
     return FFT_OK;
 }
 

@@ -1,6 +1,7 @@
 // Kernel registry shared by the per-length kernel translation units and the
-// host plan code.  Each fft_kernels.cu build (one per log2 N) defines one
-// gbfft_entry_<log2N>() returning the launch facts of its kernels.
+// host plan code.  Each fft_kernels.cu build (one per log2 N) defines
+// gbfft_entries_<log2N>(out, max) filling the launch facts of every schedule
+// variant it compiled, variant 0 first.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -8,17 +9,21 @@
 
 namespace gbfft {
 
+enum class KernelKind : int { Small = 0, Direct = 1, Ring = 2 };
+
 struct KernelEntry {
     int log2n;
-    bool small;              // one thread per signal (N <= 16)
+    int variant;
+    KernelKind kind;
     int elems_per_thread;
-    int signals_per_block;   // generic kernel: signals per tile
+    int signals_per_block;   // signals one block transforms per tile
     int threads_per_block;
     int smem_bytes;
     int num_stages;
     int radix[4];
+    int min_blocks;          // launch-bounds hint
+    int pipeline;            // bulk-copy ring depth (0 = none)
     int twiddles;            // complex64 entries in the twiddle table
-    int signals_per_warp_tile;  // small kernel: signals per warp tile
     const void* kernel_fwd;
     const void* kernel_inv;
     // Fill `host` (twiddles entries, interleaved re/im) with this schedule's table.
@@ -27,4 +32,4 @@ struct KernelEntry {
 
 }  // namespace gbfft
 
-#define GBFFT_DECLARE_ENTRY(L) gbfft::KernelEntry gbfft_entry_##L();
+#define GBFFT_DECLARE_ENTRIES(L) int gbfft_entries_##L(gbfft::KernelEntry* out, int max);

@@ -1,27 +1,48 @@
 // Radix schedules per transform length: the analogue of the paper's host-side
 // `stage_sizes` array and work-group factor (Sec. 4), fixed at compile time so
-// that every stage's register array has a static size.
+// that every stage's register array has a static size.  Several candidate
+// schedules ("variants") may exist per length; plans use variant 0 unless the
+// caller or the autotuner picks another.
 //
-// Generic Stockham kernel, one row per log2(N):
-//   X(log2N, E = complex elements per thread, S = signals per block,
-//     R0, R1, R2, R3 = stage radices first to last, 0 = no stage)
-// Threads per block = S * N / E.  The first radix R0 = E/2 (and the last, where
-// listed) lets a thread own two neighbouring butterflies, so its HBM accesses
-// are 128-bit; an index model on the host checked every exchange below for
-// shared-memory bank conflicts under the XOR swizzle of fft_device.cuh.
+// Generic Stockham kernel rows:
+//   GX(log2N, variant, E = complex elements per thread, S = signals per block,
+//      R0, R1, R2, R3 = stage radices first to last (0 = no stage),
+//      MINB = minimum resident blocks per SM requested from the compiler,
+//      PIPE = 0: stage 0 loads straight from HBM into registers;
+//             D >= 2: a ring of D shared-memory tiles filled by bulk-copy
+//             (TMA) prefetch, D-1 tiles ahead of the one being transformed)
+// Threads per block = S * N / E.  Stage 0 with R0 = E/2 (and the last stage,
+// where its radix is E/2 or less) lets a thread own neighbouring butterflies,
+// so its HBM accesses are 128-bit.  An index model on the host checked the
+// shared-memory exchanges of every row for bank conflicts under the XOR
+// swizzle of fft_device.cuh (64-bit accesses resolve per half-warp).
+//
+// One-thread-per-signal rows (N <= 32): SX(log2N, variant, warps per block).
 #pragma once
 
-#define GBFFT_SCHEDULES(X)            \
-    X(5, 16, 128, 8, 4, 0, 0)         \
-    X(6, 16, 64, 8, 8, 0, 0)          \
-    X(7, 16, 32, 8, 16, 0, 0)         \
-    X(8, 16, 16, 16, 16, 0, 0)        \
-    X(9, 16, 8, 8, 8, 8, 0)           \
-    X(10, 16, 2, 8, 16, 8, 0)         \
-    X(11, 16, 1, 8, 16, 16, 0)
+#define GBFFT_GENERIC_SCHEDULES(GX)                \
+    GX(5, 1, 16, 128, 8, 4, 0, 0, 1, 0)            \
+    GX(6, 0, 16, 64, 8, 8, 0, 0, 1, 0)             \
+    GX(7, 0, 16, 32, 8, 16, 0, 0, 1, 0)            \
+    GX(8, 0, 16, 16, 16, 16, 0, 0, 1, 0)           \
+    GX(9, 0, 16, 8, 8, 8, 8, 0, 1, 0)              \
+    GX(10, 0, 16, 2, 8, 16, 8, 0, 1, 0)            \
+    GX(10, 1, 16, 2, 8, 16, 8, 0, 4, 0)            \
+    GX(10, 2, 16, 2, 8, 16, 8, 0, 2, 2)            \
+    GX(10, 3, 16, 2, 8, 16, 8, 0, 2, 3)            \
+    GX(11, 0, 16, 1, 8, 16, 16, 0, 1, 0)           \
+    GX(11, 1, 16, 1, 8, 16, 16, 0, 4, 0)           \
+    GX(11, 2, 16, 1, 8, 16, 16, 0, 3, 2)           \
+    GX(11, 3, 16, 1, 8, 16, 16, 0, 2, 3)           \
+    GX(11, 4, 16, 2, 8, 16, 16, 0, 1, 2)
 
-// N = 2..16: one thread per signal, whole transform in registers.
-#define GBFFT_SMALL_SCHEDULES(X) X(1) X(2) X(3) X(4)
+#define GBFFT_SMALL_SCHEDULES(SX) \
+    SX(1, 0, 8)                   \
+    SX(2, 0, 8)                   \
+    SX(3, 0, 8)                   \
+    SX(4, 0, 8)                   \
+    SX(5, 0, 4)
 
 #define GBFFT_MIN_LOG2N 1
 #define GBFFT_MAX_LOG2N 11
+#define GBFFT_MAX_VARIANTS 8

@@ -22,11 +22,13 @@ from paper_2203_09384_gb300 import _abi  # noqa: E402
 POW2 = [2 ** k for k in range(1, 12)]
 
 
-def run(x_cpu: torch.Tensor, inverse=False, normalized=True, inplace=False, scale_forward=False):
+def run(x_cpu: torch.Tensor, inverse=False, normalized=True, inplace=False, scale_forward=False,
+        variant=None):
     """Copy to the GPU, run one planned transform through the C-ABI, copy back."""
     batch, n = x_cpu.shape
     d = x_cpu.to("cuda")
-    plan = gb.Plan(n, batch, inverse=inverse, normalized=normalized, scale_forward=scale_forward)
+    plan = gb.Plan(n, batch, inverse=inverse, normalized=normalized, scale_forward=scale_forward,
+                   variant=variant)
     out = d if inplace else torch.empty_like(d)
     plan.execute(d, out)
     torch.cuda.synchronize()
@@ -56,16 +58,26 @@ def _batch_for(n):
     return max(4, min(1500, 2 ** 19 // (n * n) + 700)) + 3
 
 
-@pytest.mark.parametrize("n", POW2)
+def _variants():
+    return [(n, v) for n in POW2 for v in range(gb.fft_variant_count(n))]
+
+
+@pytest.mark.parametrize("n,variant", _variants())
 @pytest.mark.parametrize("inverse", [False, True])
-def test_every_length(n, inverse):
+def test_every_length_and_schedule(n, variant, inverse):
     batch = _batch_for(n)
     x = synth.uniform(batch, n, seed=100 + n)
-    y = run(x, inverse=inverse)
-    err = max_rel_l2(to_np(y), oracle_of(x, inverse))
+    want = oracle_of(x, inverse)
+    y = run(x, inverse=inverse, variant=variant)
+    err = max_rel_l2(to_np(y), want)
     assert err <= FP32_TOL, err
     # accuracy alarm: with exact twiddles FP32 error stays near 1e-7
     assert err <= 1e-6, err
+    # a batch too small to fill one block, and one that leaves a ragged tail
+    for b in (1, 3 * 152 + 5):
+        xs = synth.uniform(b, n, seed=200 + n)
+        ys = run(xs, inverse=inverse, variant=variant)
+        assert max_rel_l2(to_np(ys), oracle_of(xs, inverse)) <= FP32_TOL
 
 
 @pytest.mark.parametrize("n", [2 ** k for k in range(3, 12)])
@@ -178,6 +190,19 @@ def test_graph_capture_and_streams():
     ref = oracle_of(x.cpu())
     assert max_rel_l2(to_np(out), ref) <= FP32_TOL
     plan.close()
+
+
+def test_variant_selection():
+    for n in POW2:
+        count = gb.fft_variant_count(n)
+        assert count >= 1
+        for v in range(count):
+            p = gb.Plan(n, 64, variant=v)
+            assert p.info().variant == v
+            p.close()
+        with pytest.raises(gb.FFTError):
+            gb.Plan(n, 64, variant=count)
+    assert gb.fft_variant_count(12) == 0
 
 
 @pytest.mark.parametrize("n", POW2)
