@@ -48,7 +48,7 @@ def test_invalid_values():
     assert _abi.fft_validate(64, 1, direction=2) == bad
     assert _abi.fft_validate(64, 1, direction=-1) == bad
     assert _abi.fft_validate(64, 1, dtype=7) == bad
-    assert _abi.fft_validate(64, 1, flags=1 << 9) == bad
+    assert _abi.fft_validate(64, 1, flags=1 << 20) == bad
     assert _abi.fft_validate(2048, 2 ** 62) == bad  # byte count overflows
 
 
