@@ -25,16 +25,16 @@
     GX(6, 0, 16, 64, 8, 8, 0, 0, 1, 0)             \
     GX(7, 0, 16, 32, 8, 16, 0, 0, 1, 0)            \
     GX(8, 0, 16, 16, 16, 16, 0, 0, 1, 0)           \
-    GX(9, 0, 16, 8, 8, 8, 8, 0, 1, 0)              \
-    GX(10, 0, 16, 2, 8, 16, 8, 0, 1, 0)            \
-    GX(10, 1, 16, 2, 8, 16, 8, 0, 4, 0)            \
-    GX(10, 2, 16, 2, 8, 16, 8, 0, 2, 2)            \
+    GX(9, 0, 16, 8, 8, 8, 8, 0, 2, 0)              \
+    GX(9, 1, 16, 8, 8, 8, 8, 0, 1, 0)              \
+    GX(10, 0, 16, 2, 8, 16, 8, 0, 2, 2)            \
+    GX(10, 1, 16, 2, 8, 16, 8, 0, 1, 0)            \
+    GX(10, 2, 16, 2, 8, 16, 8, 0, 4, 0)            \
     GX(10, 3, 16, 2, 8, 16, 8, 0, 2, 3)            \
-    GX(11, 0, 16, 1, 8, 16, 16, 0, 1, 0)           \
-    GX(11, 1, 16, 1, 8, 16, 16, 0, 4, 0)           \
-    GX(11, 2, 16, 1, 8, 16, 16, 0, 3, 2)           \
-    GX(11, 3, 16, 1, 8, 16, 16, 0, 2, 3)           \
-    GX(11, 4, 16, 2, 8, 16, 16, 0, 1, 2)
+    GX(11, 0, 16, 1, 8, 16, 16, 0, 3, 2)           \
+    GX(11, 1, 16, 1, 8, 16, 16, 0, 1, 0)           \
+    GX(11, 2, 16, 1, 8, 16, 16, 0, 2, 3)           \
+    GX(11, 3, 16, 2, 8, 16, 16, 0, 1, 2)
 
 #define GBFFT_SMALL_SCHEDULES(SX) \
     SX(1, 0, 8)                   \
