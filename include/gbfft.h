@@ -79,7 +79,9 @@ typedef enum {
     FFT_ERR_UNSUPPORTED = 7,   /* valid request this build cannot run         */
     FFT_ERR_TIMEOUT = 8,       /* a device-side bounded wait gave up          */
     FFT_ERR_DEVICE_CHECK = 9,  /* a device-side consistency check failed      */
-    FFT_ERR_NO_DEVICE = 10     /* no CUDA device, or not an sm_103 device     */
+    FFT_ERR_NO_DEVICE = 10,    /* no CUDA device, or not an sm_103 device     */
+    FFT_ERR_NOALLOC_LIMIT = 11 /* fft_execute_noalloc: the request needs more
+                                  scratch than its static array holds         */
 } fft_status_t;
 
 /*
@@ -186,6 +188,46 @@ GBFFT_API void fft_twiddle_fp32(int64_t m, int64_t k, float* out);
  */
 GBFFT_API fft_status_t fft_validate(int64_t n, int64_t batch, int direction, int dtype,
                           uint32_t flags);
+
+/*
+ * fft_execute_noalloc - the planned transform of fft_execute, for callers
+ * that cannot allocate device memory.  (The paper has no counterpart: this
+ * is an interface for library users, not part of the method.)
+ *
+ * Who needs it: a process that gives all free device memory to its own
+ * caching allocator at start-up and may not take more afterwards, or code
+ * that must not pay the implicit device-wide synchronisation that cudaMalloc
+ * and cudaFree can cause.  This call makes no plan and calls no cudaMalloc,
+ * cudaFree or other allocating routine.  Its scratch (the twiddle table of the
+ * length and an error word) lives in a file-scope static __device__ array of
+ * 4096 complex64 entries plus one 256-byte slot (about 33 KiB), which every
+ * GPU that loads the library keeps reserved until the process exits.
+ *
+ * Arguments: n, batch, direction as for fft_plan_create (dtype is FFT_C64);
+ * flags may hold FFT_FLAG_UNNORMALIZED, FFT_FLAG_SCALE_FORWARD and
+ * FFT_FLAG_VARIANT(k); in/out/stream as for fft_execute (device pointers,
+ * 16-byte aligned, equal or disjoint; the caller owns them).  The result
+ * equals fft_execute's for the same length, direction, flags and variant.
+ *
+ * Behaviour:
+ *  - The first call on a device does a one-time set-up (it looks up the
+ *    static array's device address with cudaGetSymbolAddress while that
+ *    device is current); the first call for each length, direction and
+ *    variant also queries its launch shape.  Make those first calls before
+ *    any stream capture.
+ *  - Every call enqueues two kernels on `stream`: one rewrites the shared
+ *    array (this length's twiddles, error word cleared), one transforms.  All
+ *    calls on a device share the array, which keeps the last call's
+ *    contents, so calls that may overlap on the GPU (e.g. on two streams)
+ *    race and must be serialised by the caller.
+ *  - A request whose twiddle table would not fit the array returns
+ *    FFT_ERR_NOALLOC_LIMIT (no compiled schedule needs more than 2040
+ *    entries, so every valid length fits); invalid arguments return the
+ *    codes fft_plan_create / fft_execute return; a failed launch returns
+ *    FFT_ERR_CUDA.  Device-side wait timeouts are not reported by this call.
+ */
+GBFFT_API fft_status_t fft_execute_noalloc(int64_t n, int64_t batch, int direction, uint32_t flags,
+                                           const void* in, void* out, void* stream);
 
 /* Library version, "major.minor.patch". */
 GBFFT_API const char* fft_version(void);

@@ -38,6 +38,7 @@ STATUS = {
     8: "FFT_ERR_TIMEOUT",
     9: "FFT_ERR_DEVICE_CHECK",
     10: "FFT_ERR_NO_DEVICE",
+    11: "FFT_ERR_NOALLOC_LIMIT",
 }
 STATUS_CODE = {v: k for k, v in STATUS.items()}
 
@@ -128,6 +129,8 @@ def lib() -> ctypes.CDLL:
     L.fft_get_default_variant.argtypes = [_i64]
     L.fft_plan_set_wait_limit.restype = _int
     L.fft_plan_set_wait_limit.argtypes = [_vp, ctypes.c_uint64]
+    L.fft_execute_noalloc.restype = _int
+    L.fft_execute_noalloc.argtypes = [_i64, _i64, _int, _u32, _vp, _vp, _vp]
     L.fft_twiddle_fp32.restype = None
     L.fft_twiddle_fp32.argtypes = [_i64, _i64, ctypes.POINTER(ctypes.c_float)]
     _lib = L
@@ -196,3 +199,10 @@ def fft_get_default_variant(n: int) -> int:
 
 def fft_plan_set_wait_limit(plan: int, nanoseconds: int) -> None:
     check(lib().fft_plan_set_wait_limit(plan, nanoseconds), "fft_plan_set_wait_limit")
+
+
+def fft_execute_noalloc(n: int, batch: int, direction: int, flags: int, in_ptr: int, out_ptr: int,
+                        stream: int = 0) -> None:
+    """The transform without a plan or any device allocation (static scratch)."""
+    check(lib().fft_execute_noalloc(n, batch, direction, flags, in_ptr, out_ptr, stream),
+          "fft_execute_noalloc")

@@ -39,6 +39,7 @@ def _sources():
     units = [(os.path.join(CSRC, "fft_kernels.cu"), f"fft_kernels_{k}.o", [f"-DGBFFT_LOG2N={k}"])
              for k in LOG2NS]
     units.append((os.path.join(CSRC, "gbfft_host.cu"), "gbfft_host.o", []))
+    units.append((os.path.join(CSRC, "fft_noalloc.cu"), "fft_noalloc.o", []))
     return units, deps
 
 

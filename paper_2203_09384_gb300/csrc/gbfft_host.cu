@@ -69,6 +69,18 @@ constexpr uint64_t kDefaultWaitNs = 4000000000ull;  // bounded device waits: 4 s
 
 }  // namespace
 
+namespace gbfft {
+// Registry lookup for other host translation units: the kernel entry of
+// `variant` (or of the length's current default when variant < 0), or NULL.
+const KernelEntry* lookup_entry(int log2n, int variant) {
+    if (log2n < GBFFT_MIN_LOG2N || log2n > GBFFT_MAX_LOG2N) return nullptr;
+    LengthVariants* lv = &registry()[log2n];
+    if (variant < 0) variant = lv->preferred.load();
+    if (variant >= lv->count || !lv->v[variant].kernel_fwd) return nullptr;
+    return &lv->v[variant];
+}
+}  // namespace gbfft
+
 struct gbfft_plan {
     int64_t n = 0, batch = 0;
     int log2n = 0, direction = 0, dtype = 0;
@@ -101,6 +113,8 @@ const char* fft_status_string(fft_status_t s) {
         case FFT_ERR_TIMEOUT: return "device-side wait timed out";
         case FFT_ERR_DEVICE_CHECK: return "device-side check failed";
         case FFT_ERR_NO_DEVICE: return "no usable CUDA device (sm_103 required)";
+        case FFT_ERR_NOALLOC_LIMIT:
+            return "request needs more scratch than fft_execute_noalloc's static device array holds";
     }
     return "unknown status";
 }

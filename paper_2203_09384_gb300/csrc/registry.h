@@ -30,6 +30,10 @@ struct KernelEntry {
     void (*fill_twiddles)(float* host);
 };
 
+// Registry lookup (host): the entry of `variant`, or of the length's current
+// default when variant < 0; NULL when there is none.
+const KernelEntry* lookup_entry(int log2n, int variant);
+
 }  // namespace gbfft
 
 #define GBFFT_DECLARE_ENTRIES(L) int gbfft_entries_##L(gbfft::KernelEntry* out, int max);
