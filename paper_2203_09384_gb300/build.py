@@ -33,13 +33,13 @@ def nvcc() -> str:
     return cand
 
 
-def _sources():
-    deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
+def _sources(csrc=CSRC):
+    deps = [os.path.join(csrc, f) for f in os.listdir(csrc) if f.endswith((".cuh", ".h"))]
     deps.append(os.path.join(INCLUDE, "gbfft.h"))
-    units = [(os.path.join(CSRC, "fft_kernels.cu"), f"fft_kernels_{k}.o", [f"-DGBFFT_LOG2N={k}"])
+    units = [(os.path.join(csrc, "fft_kernels.cu"), f"fft_kernels_{k}.o", [f"-DGBFFT_LOG2N={k}"])
              for k in LOG2NS]
-    units.append((os.path.join(CSRC, "gbfft_host.cu"), "gbfft_host.o", []))
-    units.append((os.path.join(CSRC, "fft_noalloc.cu"), "fft_noalloc.o", []))
+    units.append((os.path.join(csrc, "gbfft_host.cu"), "gbfft_host.o", []))
+    units.append((os.path.join(csrc, "fft_noalloc.cu"), "fft_noalloc.o", []))
     return units, deps
 
 
@@ -50,11 +50,11 @@ def _stale(target, inputs):
     return any(os.path.getmtime(i) > t for i in inputs)
 
 
-def _compile(src, obj, defs, deps, verbose):
-    out = os.path.join(BUILD, "obj", obj)
+def _compile(src, obj, defs, deps, verbose, build_dir=BUILD):
+    out = os.path.join(build_dir, "obj", obj)
     if not _stale(out, [src] + deps):
         return out, False
-    cmd = [nvcc(), *ARCH, *CFLAGS, *defs, "-c", src, "-o", out + ".tmp"]
+    cmd = [nvcc(), *ARCH, *CFLAGS, "-I", os.path.dirname(src), *defs, "-c", src, "-o", out + ".tmp"]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
     r = subprocess.run(cmd, capture_output=True, text=True)
@@ -66,27 +66,30 @@ def _compile(src, obj, defs, deps, verbose):
     return out, True
 
 
-def build(jobs: int | None = None, verbose: bool = False, force: bool = False) -> str:
-    """Compile every kernel unit and link ``_build/libgbfft.so``; returns its path."""
-    os.makedirs(os.path.join(BUILD, "obj"), exist_ok=True)
-    units, deps = _sources()
+def build(jobs: int | None = None, verbose: bool = False, force: bool = False,
+          csrc: str = CSRC, build_dir: str = BUILD) -> str:
+    """Compile every kernel unit of ``csrc`` and link ``<build_dir>/libgbfft.so``
+    (defaults: this package's sources into ``_build/``); returns its path."""
+    lib_path = os.path.join(build_dir, "libgbfft.so")
+    os.makedirs(os.path.join(build_dir, "obj"), exist_ok=True)
+    units, deps = _sources(csrc)
     if force:
         for _, obj, _ in units:
-            p = os.path.join(BUILD, "obj", obj)
+            p = os.path.join(build_dir, "obj", obj)
             if os.path.exists(p):
                 os.remove(p)
     jobs = jobs or min(len(units), os.cpu_count() or 4)
     with cf.ThreadPoolExecutor(max_workers=jobs) as ex:
-        results = list(ex.map(lambda u: _compile(u[0], u[1], u[2], deps, verbose), units))
+        results = list(ex.map(lambda u: _compile(u[0], u[1], u[2], deps, verbose, build_dir), units))
     objs = [r[0] for r in results]
-    if any(r[1] for r in results) or _stale(LIB, objs):
-        tmp = LIB + f".tmp{os.getpid()}"
+    if any(r[1] for r in results) or _stale(lib_path, objs):
+        tmp = lib_path + f".tmp{os.getpid()}"
         cmd = [nvcc(), *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib_path)
+    return lib_path
 
 
 if __name__ == "__main__":
