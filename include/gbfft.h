@@ -95,6 +95,27 @@ typedef enum {
 GBFFT_API fft_status_t fft_plan_create(int64_t n, int64_t batch, int direction, int dtype,
                              fft_plan_t* plan);
 
+/*
+ * Ragged batch: `count` signals of mixed power-of-two lengths packed back to
+ * back.  offsets_host[0..count] (host memory, int64, read only during this
+ * call) gives signal i the elements [offsets_host[i], offsets_host[i+1]) of the
+ * buffers later passed to fft_execute; every length must be a power of two in
+ * [2, 2048] and offsets_host[0] must be even (so every signal starts 16-byte
+ * aligned).  The plan buckets the signals by length into tiles and uploads a
+ * device work list; fft_execute then clears the plan's work counter with a
+ * memset node and launches ONE persistent kernel whose blocks take tiles from
+ * the list (graph-capturable).  Because of that counter, a ragged plan must
+ * not be executed on two streams at once.  flags: FFT_FLAG_UNNORMALIZED,
+ * FFT_FLAG_SCALE_FORWARD, FFT_FLAG_VARIANT(k) with k < fft_ragged_variant_count().
+ * Errors: FFT_ERR_INVALID_SIZE (a length), FFT_ERR_INVALID_VALUE, FFT_ERR_MISALIGNED
+ * (odd offsets_host[0]), FFT_ERR_ALLOC, FFT_ERR_CUDA, FFT_ERR_NO_DEVICE.
+ */
+GBFFT_API fft_status_t fft_plan_create_ragged(const int64_t* offsets_host, int64_t count, int direction,
+                                              int dtype, uint32_t flags, fft_plan_t* plan);
+
+/* Number of compiled schedule variants of the ragged kernel. */
+GBFFT_API int fft_ragged_variant_count(void);
+
 /* As fft_plan_create, with FFT_FLAG_* bits in `flags`. */
 GBFFT_API fft_status_t fft_plan_create_ex(int64_t n, int64_t batch, int direction, int dtype,
                                 uint32_t flags, fft_plan_t* plan);
@@ -140,7 +161,9 @@ typedef struct {
     int variant;            /* schedule variant of this length in use           */
     int pipeline;           /* bulk-copy (TMA) prefetch ring depth, 0 = none     */
     int min_blocks;         /* launch-bounds residency hint                     */
-    int kernel_kind;        /* 0 one thread per signal, 1 direct, 2 TMA ring    */
+    int kernel_kind;        /* 0 one thread per signal, 1 direct, 2 TMA ring,
+                               3 ragged persistent work list                    */
+    int64_t work_items;     /* ragged plans: tiles in the device work list      */
     int64_t grid;           /* blocks launched (persistent grid-stride loop)    */
     int64_t smem_bytes;     /* dynamic shared memory per block                  */
     int64_t twiddle_count;  /* complex64 entries in the plan's twiddle table    */

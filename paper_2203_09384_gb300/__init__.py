@@ -18,13 +18,15 @@ import torch
 
 from ._abi import (FFT_C64, FFT_C64_TC_BF16, FFT_C64_TC_F16, FFT_FLAG_SCALE_FORWARD,  # noqa: F401
                    FFT_FLAG_UNNORMALIZED, FFT_FLAG_VARIANT, fft_get_default_variant,
+                   fft_plan_create_ragged, fft_ragged_variant_count,
                    fft_set_default_variant, fft_variant_count,
                    FFT_FORWARD, FFT_INVERSE, FFTError, STATUS, fft_execute, fft_plan_create,
                    fft_plan_create_ex, fft_plan_destroy, fft_plan_get_error, fft_plan_get_info,
                    fft_validate, lib)
 
-__all__ = ["Plan", "fft", "ifft", "FFTFunction", "fft_plan_create", "fft_plan_create_ex",
-           "fft_execute", "fft_plan_destroy", "fft_plan_get_error", "FFTError", "lib"]
+__all__ = ["Plan", "RaggedPlan", "fft", "ifft", "FFTFunction", "IFFTFunction", "fft_plan_create",
+           "fft_plan_create_ex", "fft_plan_create_ragged", "fft_execute", "fft_plan_destroy",
+           "fft_plan_get_error", "FFTError", "lib"]
 
 _DTYPES = {"c64": FFT_C64, "tc_f16": FFT_C64_TC_F16, "tc_bf16": FFT_C64_TC_BF16}
 
@@ -76,6 +78,70 @@ class Plan:
 
     def error(self) -> int:
         return fft_plan_get_error(self.handle)
+
+    def close(self):
+        if self.handle:
+            fft_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class RaggedPlan:
+    """Mixed-length batch: signal i occupies elements [offsets[i], offsets[i+1])
+    of a flat complex64 buffer; one persistent launch transforms them all."""
+
+    def __init__(self, offsets, inverse: bool = False, normalized: bool = True,
+                 scale_forward: bool = False, variant: int | None = None, device=None):
+        offs = [int(v) for v in (offsets.tolist() if hasattr(offsets, "tolist") else offsets)]
+        if len(offs) < 1:
+            raise ValueError("offsets needs count + 1 entries")
+        self.offsets = offs
+        self.count = len(offs) - 1
+        self.total = offs[-1]
+        self.inverse = inverse
+        self.device = torch.device(device) if device is not None else torch.device(
+            "cuda", torch.cuda.current_device())
+        flags = 0 if normalized else FFT_FLAG_UNNORMALIZED
+        if scale_forward and not inverse:
+            flags |= FFT_FLAG_SCALE_FORWARD
+        if variant is not None:
+            flags |= FFT_FLAG_VARIANT(variant)
+        self.handle = None
+        with torch.cuda.device(self.device):
+            self.handle = fft_plan_create_ragged(offs, FFT_INVERSE if inverse else FFT_FORWARD,
+                                                 FFT_C64, flags)
+
+    def info(self):
+        return fft_plan_get_info(self.handle)
+
+    def execute(self, x: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        if x.dtype != torch.complex64 or not x.is_cuda or not x.is_contiguous():
+            raise TypeError("expected a contiguous complex64 CUDA tensor")
+        if x.numel() < self.total:
+            raise ValueError(f"buffer has {x.numel()} elements, offsets reach {self.total}")
+        if out is None:
+            out = torch.empty_like(x)
+        with torch.cuda.device(x.device):
+            s = stream if stream is not None else torch.cuda.current_stream(x.device)
+            fft_execute(self.handle, x.data_ptr(), out.data_ptr(), s.cuda_stream)
+        return out
+
+    def capture(self, x: torch.Tensor, out: torch.Tensor) -> "torch.cuda.CUDAGraph":
+        """Capture execute(x, out) (counter reset + persistent kernel) in a CUDA graph."""
+        s = torch.cuda.Stream(device=x.device)
+        s.wait_stream(torch.cuda.current_stream(x.device))
+        with torch.cuda.stream(s):
+            self.execute(x, out)  # warm-up outside the capture
+        torch.cuda.current_stream(x.device).wait_stream(s)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            self.execute(x, out)
+        return g
 
     def close(self):
         if self.handle:

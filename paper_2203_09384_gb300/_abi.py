@@ -71,6 +71,7 @@ class PlanInfo(ctypes.Structure):
         ("pipeline", ctypes.c_int),
         ("min_blocks", ctypes.c_int),
         ("kernel_kind", ctypes.c_int),
+        ("work_items", ctypes.c_int64),
         ("grid", ctypes.c_int64),
         ("smem_bytes", ctypes.c_int64),
         ("twiddle_count", ctypes.c_int64),
@@ -129,6 +130,10 @@ def lib() -> ctypes.CDLL:
     L.fft_get_default_variant.argtypes = [_i64]
     L.fft_plan_set_wait_limit.restype = _int
     L.fft_plan_set_wait_limit.argtypes = [_vp, ctypes.c_uint64]
+    L.fft_plan_create_ragged.restype = _int
+    L.fft_plan_create_ragged.argtypes = [ctypes.POINTER(_i64), _i64, _int, _int, _u32, ctypes.POINTER(_vp)]
+    L.fft_ragged_variant_count.restype = _int
+    L.fft_ragged_variant_count.argtypes = []
     L.fft_execute_noalloc.restype = _int
     L.fft_execute_noalloc.argtypes = [_i64, _i64, _int, _u32, _vp, _vp, _vp]
     L.fft_twiddle_fp32.restype = None
@@ -206,3 +211,17 @@ def fft_execute_noalloc(n: int, batch: int, direction: int, flags: int, in_ptr: 
     """The transform without a plan or any device allocation (static scratch)."""
     check(lib().fft_execute_noalloc(n, batch, direction, flags, in_ptr, out_ptr, stream),
           "fft_execute_noalloc")
+
+
+def fft_plan_create_ragged(offsets, direction: int = FFT_FORWARD, dtype: int = FFT_C64,
+                           flags: int = 0) -> int:
+    """offsets: sequence of count+1 int64 element offsets (host)."""
+    arr = (ctypes.c_int64 * len(offsets))(*[int(v) for v in offsets])
+    h = _vp()
+    check(lib().fft_plan_create_ragged(arr, len(offsets) - 1, direction, dtype, flags, ctypes.byref(h)),
+          "fft_plan_create_ragged")
+    return h.value
+
+
+def fft_ragged_variant_count() -> int:
+    return lib().fft_ragged_variant_count()

@@ -40,6 +40,7 @@ def _sources(csrc=CSRC):
              for k in LOG2NS]
     units.append((os.path.join(csrc, "gbfft_host.cu"), "gbfft_host.o", []))
     units.append((os.path.join(csrc, "fft_noalloc.cu"), "fft_noalloc.o", []))
+    units.append((os.path.join(csrc, "fft_ragged.cu"), "fft_ragged.o", []))
     return units, deps
 
 

@@ -296,7 +296,7 @@ struct Cfg {
     static constexpr int kTwiddles = tw_off(M);
     static_assert(N % E == 0, "E must divide N");
     static_assert(ns(M) == N, "radices must multiply to N");
-    static_assert(M >= 2, "generic kernel needs at least two stages");
+    static_assert(M >= 1, "at least one stage");
     static_assert(E % R0 == 0 && (R1 == 0 || E % R1 == 0) && (R2 == 0 || E % R2 == 0) &&
                       (R3 == 0 || E % R3 == 0),
                   "every radix must divide E");
@@ -497,7 +497,7 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
                              float scale, int* err, uint64_t wait_ns) {
     constexpr int D = C::PIPE;
     constexpr int TILE = C::S * C::N;
-    extern __shared__ __align__(128) float2 smem[];
+    extern __shared__ __align__(16) float2 smem[];
     float2* ring = smem + C::kSmemElems;
     uint64_t* bars = reinterpret_cast<uint64_t*>(ring + D * TILE);
     const int tid = threadIdx.x;

@@ -94,6 +94,7 @@ struct gbfft_plan {
     int64_t grid = 0;
     float scale = 1.0f;
     uint64_t wait_ns = kDefaultWaitNs;
+    gbfft::RaggedState* ragged = nullptr;  // set for mixed-length plans
 };
 
 extern "C" {
@@ -266,12 +267,55 @@ fft_status_t fft_plan_create_ex(int64_t n, int64_t batch, int direction, int dty
     return FFT_OK;
 }
 
+int fft_ragged_variant_count(void) { return gbfft::ragged_variant_count(); }
+
+fft_status_t fft_plan_create_ragged(const int64_t* offsets_host, int64_t count, int direction, int dtype,
+                                    uint32_t flags, fft_plan_t* plan) {
+    if (!plan) return FFT_ERR_INVALID_VALUE;
+    if (direction != FFT_FORWARD && direction != FFT_INVERSE) return FFT_ERR_INVALID_VALUE;
+    if (dtype != FFT_C64 && dtype != FFT_C64_TC_F16 && dtype != FFT_C64_TC_BF16) return FFT_ERR_INVALID_VALUE;
+    if (flags & ~kKnownFlags) return FFT_ERR_INVALID_VALUE;
+    if (dtype != FFT_C64) return FFT_ERR_UNSUPPORTED;
+    if (count < 0 || (count > 0 && !offsets_host)) return FFT_ERR_INVALID_VALUE;
+    int ndev = 0, dev = 0, major = 0, minor = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return FFT_ERR_NO_DEVICE;
+    }
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev) != cudaSuccess)
+        return FFT_ERR_CUDA;
+    if (major != 10 || minor != 3) return FFT_ERR_NO_DEVICE;
+    gbfft_plan* p = new (std::nothrow) gbfft_plan();
+    if (!p) return FFT_ERR_ALLOC;
+    int64_t grid = 0;
+    fft_status_t st = gbfft::ragged_create(offsets_host, count, direction, flags, &p->ragged, &grid);
+    if (st != FFT_OK) {
+        delete p;
+        return st;
+    }
+    p->batch = count;
+    p->direction = direction;
+    p->dtype = dtype;
+    p->flags = flags;
+    p->device = dev;
+    p->grid = grid;
+    *plan = p;
+    return FFT_OK;
+}
+
 fft_status_t fft_plan_create(int64_t n, int64_t batch, int direction, int dtype, fft_plan_t* plan) {
     return fft_plan_create_ex(n, batch, direction, dtype, 0u, plan);
 }
 
 fft_status_t fft_execute(fft_plan_t p, const void* in, void* out, void* stream) {
     if (!p) return FFT_ERR_INVALID_VALUE;
+    if (p->ragged) {
+        int dev = -1;
+        if (cudaGetDevice(&dev) != cudaSuccess || dev != p->device) return FFT_ERR_INVALID_VALUE;
+        return gbfft::ragged_execute(p->ragged, in, out, stream);
+    }
     if (p->batch == 0) return FFT_OK;
     if (!in || !out) return FFT_ERR_INVALID_VALUE;
     if (((uintptr_t)in & 15) || ((uintptr_t)out & 15)) return FFT_ERR_MISALIGNED;
@@ -308,6 +352,7 @@ fft_status_t fft_execute(fft_plan_t p, const void* in, void* out, void* stream) 
 
 fft_status_t fft_plan_get_error(fft_plan_t p) {
     if (!p) return FFT_ERR_INVALID_VALUE;
+    if (!p->d_error) return cudaDeviceSynchronize() == cudaSuccess ? FFT_OK : FFT_ERR_CUDA;
     int word = 0;
     if (cudaMemcpy(&word, p->d_error, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return FFT_ERR_CUDA;
     if (word != 0) {
@@ -321,6 +366,7 @@ fft_status_t fft_plan_destroy(fft_plan_t p) {
     if (!p) return FFT_OK;
     fft_status_t st = FFT_OK;
     if (p->d_twiddles && cudaFree(p->d_twiddles) != cudaSuccess) st = FFT_ERR_CUDA;
+    gbfft::ragged_destroy(p->ragged);
     delete p;
     return st;
 }
@@ -328,6 +374,13 @@ fft_status_t fft_plan_destroy(fft_plan_t p) {
 fft_status_t fft_plan_get_info(fft_plan_t p, fft_plan_info_t* info) {
     if (!p || !info) return FFT_ERR_INVALID_VALUE;
     memset(info, 0, sizeof(*info));
+    if (p->ragged) {
+        info->direction = p->direction;
+        info->dtype = p->dtype;
+        info->flags = p->flags;
+        gbfft::ragged_info(p->ragged, info);
+        return FFT_OK;
+    }
     const KernelEntry* e = p->entry;
     info->n = p->n;
     info->batch = p->batch;
@@ -368,13 +421,13 @@ int fft_get_default_variant(int64_t n) {
 }
 
 fft_status_t fft_plan_set_wait_limit(fft_plan_t p, uint64_t nanoseconds) {
-    if (!p || nanoseconds == 0) return FFT_ERR_INVALID_VALUE;
+    if (!p || nanoseconds == 0 || p->ragged) return FFT_ERR_INVALID_VALUE;
     p->wait_ns = nanoseconds;
     return FFT_OK;
 }
 
 fft_status_t fft_plan_get_twiddles(fft_plan_t p, void* host_out, int64_t count) {
-    if (!p || (!host_out && count > 0)) return FFT_ERR_INVALID_VALUE;
+    if (!p || (!host_out && count > 0) || p->ragged) return FFT_ERR_INVALID_VALUE;
     if (count != p->entry->twiddles) return FFT_ERR_INVALID_VALUE;
     if (count == 0) return FFT_OK;
     if (cudaMemcpy(host_out, p->d_twiddles, (size_t)count * 8, cudaMemcpyDeviceToHost) != cudaSuccess)

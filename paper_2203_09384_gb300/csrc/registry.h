@@ -7,6 +7,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "../../include/gbfft.h"
+
 namespace gbfft {
 
 enum class KernelKind : int { Small = 0, Direct = 1, Ring = 2 };
@@ -33,6 +35,15 @@ struct KernelEntry {
 // Registry lookup (host): the entry of `variant`, or of the length's current
 // default when variant < 0; NULL when there is none.
 const KernelEntry* lookup_entry(int log2n, int variant);
+
+// Ragged (mixed-length) plans, implemented in fft_ragged.cu.
+struct RaggedState;
+int ragged_variant_count();
+fft_status_t ragged_create(const int64_t* offsets, int64_t count, int direction, uint32_t flags,
+                           RaggedState** out, int64_t* grid_out);
+fft_status_t ragged_execute(RaggedState* st, const void* in, void* out, void* stream);
+void ragged_info(const RaggedState* st, fft_plan_info_t* info);
+void ragged_destroy(RaggedState* st);
 
 }  // namespace gbfft
 
