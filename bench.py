@@ -176,6 +176,132 @@ def cpu_baseline(budget_s: float = 12.0, threads: int | None = None):
             "per_n_gbs": detail}
 
 
+def _time_ms(fn, stream, reps: int = 10, warmup: int = 3) -> float:
+    import torch
+    for _ in range(warmup):
+        fn()
+    ts = []
+    for _ in range(reps):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        b.synchronize()
+        ts.append(a.elapsed_time(b))
+    return statistics.median(ts)
+
+
+def run_extras(dev, stream, peak):
+    """The other workloads of the hot path, each on its own synthetic data:
+    the adjoint (autograd backward), ragged mixed lengths in one graph-captured
+    launch, and FP16/BF16 tensor-core radix-16 stages against FP32."""
+    import torch
+
+    import paper_2203_09384_gb300 as gb
+    import synth
+    from paper_2203_09384_gb300 import autotune
+
+    out = {}
+    gbs = lambda elems, ms: round(BYTES_PER_ELEM * elems / (ms * 1e-3) / 1e9, 1)  # noqa: E731
+    # -- adjoint: loss = sum |W * FFT(x)|^2, N = 1024, batch = 65536, seed 2
+    n, b = 1024, 65536
+    g = torch.Generator(device=dev)
+    g.manual_seed(2)
+    x = torch.view_as_complex(torch.randn(b, n, 2, generator=g, device=dev))
+    w = torch.view_as_complex(torch.randn(b, n, 2, generator=g, device=dev))
+    fwd = gb.Plan(n, b, device=dev)
+    adj = gb.Plan(n, b, inverse=True, normalized=False, device=dev)
+    y = torch.empty_like(x)
+    ms_f = _time_ms(lambda: fwd.execute(x, y), stream)
+    ms_b = _time_ms(lambda: adj.execute(y, x), stream)
+    xg = x.clone().requires_grad_(True)
+
+    def step():
+        xg.grad = None
+        loss = (torch.abs(w * gb.FFTFunction.apply(xg)) ** 2).sum()
+        loss.backward()
+
+    ms_step = _time_ms(step, stream, reps=5)
+    out["adjoint"] = {"workload": "loss=sum|W*FFT(x)|^2, N=1024, batch=65536, x,W ~ CN(0,1), seed 2",
+                      "forward_gbs": gbs(n * b, ms_f), "adjoint_backward_gbs": gbs(n * b, ms_b),
+                      "forward_ms": round(ms_f, 4), "adjoint_ms": round(ms_b, 4),
+                      "autograd_step_ms": round(ms_step, 4),
+                      "note": "step = forward FFT + torch loss ops + adjoint FFT kernel"}
+    del x, w, y, xg
+    # -- ragged: 20000 signals, lengths 2^U{4..11}, seed 3, one launch in a CUDA graph
+    lengths = synth.ragged_lengths(20000, seed=3)
+    offs = synth.ragged_offsets(lengths)
+    xr = synth.ragged_uniform(lengths, seed=3).to(dev)
+    yr = torch.empty_like(xr)
+    tuned = autotune.tune_ragged(offs.numpy(), xr, yr, reps=10)
+    rp = gb.RaggedPlan(offs.numpy(), variant=tuned["best"], device=dev)
+    total = int(offs[-1])
+    # the same signals grouped by length: one plain launch per length
+    grouped, pos = [], 0
+    for L in sorted(set(lengths.tolist())):
+        cnt = int((lengths == L).sum())
+        grouped.append((L, cnt, pos))
+        pos += L * cnt
+    plans = [(gb.Plan(L, cnt, device=dev), p0, L * cnt) for L, cnt, p0 in grouped]
+    # 163 MB of traffic would sit in the 129 MB L2 after one replay: rotate
+    # through 8 buffer pairs (1.3 GB) so every replay reads and writes HBM
+    rot = 8
+    bufs = [(xr.clone(), torch.empty_like(xr)) for _ in range(rot)]
+
+    def capture(fn):
+        side = torch.cuda.Stream(device=dev)
+        side.wait_stream(stream)
+        with torch.cuda.stream(side):
+            fn()
+        stream.wait_stream(side)
+        gr = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(gr):
+            fn()
+        return gr
+
+    rg = [capture(lambda a=a, o=o: rp.execute(a, o)) for a, o in bufs]
+    pg = [capture(lambda a=a, o=o: [p.execute(a[p0:p0 + m], o[p0:p0 + m]) for p, p0, m in plans])
+          for a, o in bufs]
+    state = {"i": 0}
+
+    def replay(graphs):
+        graphs[state["i"] % rot].replay()
+        state["i"] += 1
+
+    ms_r = _time_ms(lambda: replay(rg), stream, reps=40, warmup=rot)
+    ms_p = _time_ms(lambda: replay(pg), stream, reps=40, warmup=rot)
+    out["ragged"] = {"workload": "20000 C2C FFTs, lengths 2^U{4..11} (seed 3), packed, U[-1,1]",
+                     "elements": total, "variant": tuned["best"], "tuner_ms": tuned["ms"],
+                     "ragged_graph_ms": round(ms_r, 4), "ragged_gbs": gbs(total, ms_r),
+                     "plain_per_length_graph_ms": round(ms_p, 4), "plain_per_length_gbs": gbs(total, ms_p),
+                     "l2": "8 rotating buffer pairs (1.3 GB) so replays are not served from L2",
+                     "launches": {"ragged": 1, "plain": len(plans)}}
+    del rg, pg, bufs
+    del xr, yr
+    # -- precision: FP16/BF16 tensor-core radix-16 vs FP32, N in {256, 2048}, batch 2^17, seed 4
+    prec = {}
+    for n in (256, 2048):
+        b = 2 ** 17
+        xs, _ = synth.scaled_normal(b, n, seed=4, device=dev)
+        ref = torch.empty_like(xs)
+        res = {}
+        for dt in ("c64", "tc_f16", "tc_bf16"):
+            p = gb.Plan(n, b, dtype=dt, device=dev)
+            o = torch.empty_like(xs)
+            ms = _time_ms(lambda: p.execute(xs, o), stream)
+            if dt == "c64":
+                ref.copy_(o)
+            d = torch.linalg.vector_norm(o - ref, dim=1) / torch.linalg.vector_norm(ref, dim=1)
+            res[dt] = {"gbs": gbs(n * b, ms), "frac": round(gbs(n * b, ms) / peak, 4), "ms": round(ms, 4),
+                       "max_rel_l2_vs_fp32_path": float(d.max()), "tc_stages": int(p.info().tc != 0)}
+        prec[str(n)] = res
+    out["precision"] = {"workload": "CN(0,1) x 10^U(-3,3) per signal (seed 4), batch 2^17",
+                        "note": "error against the FP64 oracle is in the test suite (bound 5e-3); "
+                                "here: difference from the FP32 path on the same GPU", "by_n": prec}
+    return out
+
+
 def run_reference(args):
     """The reference arm: the FP64 CPU oracle on the host cores, on this bench's
     workload, each step a bounded sample."""
@@ -336,6 +462,8 @@ def run_ours(args):
         "gpu_launches": args.steps * len(LOG2NS),
         "clocks": clocks,
     }
+    if not args.no_extras:
+        line["extra"] = run_extras(dev, stream, peak)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line))
@@ -352,6 +480,8 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the adjoint / ragged / tensor-core workloads")
     ap.add_argument("--only-n", default="", help="comma list of lengths (profiling runs)")
     ap.add_argument("--elems", type=int, default=0, help="elements per length (profiling runs)")
     args = ap.parse_args(argv)

@@ -164,6 +164,8 @@ typedef struct {
     int kernel_kind;        /* 0 one thread per signal, 1 direct, 2 TMA ring,
                                3 ragged persistent work list                    */
     int64_t work_items;     /* ragged plans: tiles in the device work list      */
+    int tc;                 /* radix-16 stages on tensor cores: 0 no (FP32),
+                               1 FP16 operands, 2 BF16 operands                 */
     int64_t grid;           /* blocks launched (persistent grid-stride loop)    */
     int64_t smem_bytes;     /* dynamic shared memory per block                  */
     int64_t twiddle_count;  /* complex64 entries in the plan's twiddle table    */
@@ -175,13 +177,17 @@ GBFFT_API fft_status_t fft_plan_get_info(fft_plan_t plan, fft_plan_info_t* info)
  * Schedule variants.  Each length has one or more compiled radix schedules /
  * launch shapes (the analogue of the paper's host-chosen stage_sizes and
  * work-group factor, Sec. 4).  fft_variant_count returns how many (0 for an
- * invalid length); fft_set_default_variant chooses the one later plans of
+ * invalid length); fft_set_default_variant chooses the FP32 one later plans of
  * that length use (process-wide; the autotuner calls it); plans already made
  * keep theirs.  fft_get_default_variant returns the current choice or -1.
  */
 GBFFT_API int fft_variant_count(int64_t n);
 GBFFT_API fft_status_t fft_set_default_variant(int64_t n, int variant);
 GBFFT_API int fft_get_default_variant(int64_t n);
+/* The dtype (FFT_C64, FFT_C64_TC_F16 or FFT_C64_TC_BF16) that variant k of
+ * length n computes in, or -1 when there is no such variant.  Plans accept a
+ * variant only with its own dtype. */
+GBFFT_API int fft_variant_dtype(int64_t n, int variant);
 
 /*
  * Wall-time limit for the device-side waits of this plan's kernels (the

@@ -18,7 +18,8 @@ import torch
 
 from ._abi import (FFT_C64, FFT_C64_TC_BF16, FFT_C64_TC_F16, FFT_FLAG_SCALE_FORWARD,  # noqa: F401
                    FFT_FLAG_UNNORMALIZED, FFT_FLAG_VARIANT, fft_get_default_variant,
-                   fft_plan_create_ragged, fft_ragged_variant_count,
+                   fft_plan_create_ragged, fft_ragged_variant_count, fft_variant_dtype,
+                   DTYPE_NAMES,
                    fft_set_default_variant, fft_variant_count,
                    FFT_FORWARD, FFT_INVERSE, FFTError, STATUS, fft_execute, fft_plan_create,
                    fft_plan_create_ex, fft_plan_destroy, fft_plan_get_error, fft_plan_get_info,

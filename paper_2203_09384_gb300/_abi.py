@@ -72,6 +72,7 @@ class PlanInfo(ctypes.Structure):
         ("min_blocks", ctypes.c_int),
         ("kernel_kind", ctypes.c_int),
         ("work_items", ctypes.c_int64),
+        ("tc", ctypes.c_int),
         ("grid", ctypes.c_int64),
         ("smem_bytes", ctypes.c_int64),
         ("twiddle_count", ctypes.c_int64),
@@ -128,6 +129,8 @@ def lib() -> ctypes.CDLL:
     L.fft_set_default_variant.argtypes = [_i64, _int]
     L.fft_get_default_variant.restype = _int
     L.fft_get_default_variant.argtypes = [_i64]
+    L.fft_variant_dtype.restype = _int
+    L.fft_variant_dtype.argtypes = [_i64, _int]
     L.fft_plan_set_wait_limit.restype = _int
     L.fft_plan_set_wait_limit.argtypes = [_vp, ctypes.c_uint64]
     L.fft_plan_create_ragged.restype = _int
@@ -225,3 +228,10 @@ def fft_plan_create_ragged(offsets, direction: int = FFT_FORWARD, dtype: int = F
 
 def fft_ragged_variant_count() -> int:
     return lib().fft_ragged_variant_count()
+
+
+DTYPE_NAMES = {FFT_C64: "c64", FFT_C64_TC_F16: "tc_f16", FFT_C64_TC_BF16: "tc_bf16"}
+
+
+def fft_variant_dtype(n: int, variant: int) -> int:
+    return lib().fft_variant_dtype(n, variant)

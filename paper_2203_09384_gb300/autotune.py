@@ -64,6 +64,8 @@ def tune_lengths(lengths=LENGTHS, elems: int = 2 ** 26, reps: int = 7, apply: bo
     for n in lengths:
         timings = {}
         for v in range(_abi.fft_variant_count(n)):
+            if _abi.fft_variant_dtype(n, v) != _abi.FFT_C64:
+                continue  # tensor-core variants are chosen by dtype, not tuned against FP32
             p = Plan(n, elems // n, variant=v, device=dev)
             timings[v] = _time(lambda: p.execute(x, out), reps)
             if p.error() != 0:

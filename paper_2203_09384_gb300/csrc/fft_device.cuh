@@ -22,6 +22,8 @@
 // grid-stride loop walks tiles of S signals.
 #pragma once
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -262,7 +264,7 @@ constexpr int kErrTimeout = 8;
 // ---------------------------------------------------------------------------
 // Compile-time schedule
 // ---------------------------------------------------------------------------
-template <int LOG2N_, int E_, int S_, int R0, int R1, int R2, int R3, int MINB_ = 1, int PIPE_ = 0>
+template <int LOG2N_, int E_, int S_, int R0, int R1, int R2, int R3, int MINB_ = 1, int PIPE_ = 0, int TC_ = 0>
 struct Cfg {
     static constexpr int LOG2N = LOG2N_;
     static constexpr int N = 1 << LOG2N_;
@@ -277,7 +279,13 @@ struct Cfg {
     static constexpr int kBuffers = kWarpLocal ? 1 : 2;
     static constexpr int kSmemElems = kBuffers * S * N;           // exchange buffers
     static constexpr int kRingElems = PIPE * S * N;               // prefetch ring
-    static constexpr int kSmemBytes = (kSmemElems + kRingElems) * 8 + (PIPE > 0 ? 8 * PIPE : 0);
+    // 0: FP32 butterflies; 1 / 2: radix-16 stages on FP16 / BF16 tensor cores
+    static constexpr int TC = TC_;
+    static constexpr int kTcTiles = NT / 128;  // 128-row MMA tiles per radix-16 stage
+    static constexpr int kTcCols = 32 * kTcTiles;  // TMEM columns (FP32 accumulators)
+    static constexpr int kTcOffset = (((kSmemElems + kRingElems) * 8 + 8 * PIPE) + 127) / 128 * 128;
+    static constexpr int kTcBytes = TC ? kTcTiles * 8192 + 2048 + 128 : 0;
+    static constexpr int kSmemBytes = TC ? kTcOffset + kTcBytes : (kSmemElems + kRingElems) * 8 + 8 * PIPE;
     __host__ __device__ static constexpr int radix(int s) {
         return s == 0 ? R0 : s == 1 ? R1 : s == 2 ? R2 : R3;
     }
@@ -297,13 +305,236 @@ struct Cfg {
     static_assert(N % E == 0, "E must divide N");
     static_assert(ns(M) == N, "radices must multiply to N");
     static_assert(M >= 1, "at least one stage");
-    static_assert(E % R0 == 0 && (R1 == 0 || E % R1 == 0) && (R2 == 0 || E % R2 == 0) &&
-                      (R3 == 0 || E % R3 == 0),
+    static_assert(E % R0 == 0 && E % (R1 ? R1 : 1) == 0 && E % (R2 ? R2 : 1) == 0 && E % (R3 ? R3 : 1) == 0,
                   "every radix must divide E");
     static_assert(32 % T == 0 || T % 32 == 0, "T must tile warps");
     static_assert(PIPE == 0 || (PIPE >= 2 && !kWarpLocal),
                   "the bulk-copy ring needs block-wide exchanges (T > 32)");
+    static_assert(TC == 0 || (E == 16 && NT % 128 == 0 && (kTcCols == 32 || kTcCols == 64 || kTcCols == 128)),
+                  "tensor-core radix-16 stages need one 16-point butterfly per thread and 128-row tiles");
 };
+
+// ---------------------------------------------------------------------------
+// Tensor-core radix-16 stage (tcgen05, FP16 or BF16 operands, FP32 in TMEM)
+//
+// A batch of 16-point DFTs Y = F X is one real matrix product: row m of A is
+// one butterfly's inputs [Re x_0..15, Im x_0..15] (K = 32), and the 32 x 32
+// real form of F (stored N x K) gives row m of D = [Re y_0..15, Im y_0..15]:
+//   Re y_q = sum_r  c_qr Re x_r + s_qr Im x_r,   Im y_q = sum_r -s_qr Re x_r + c_qr Im x_r,
+// with c_qr + i s_qr = e^{+2 pi i qr/16} (so F_qr = c_qr - i s_qr).  A block of
+// 128 threads is one M = 128 tile: each thread writes its own row, one thread
+// issues the MMA (two K = 16 steps), and after tcgen05.ld each thread holds its
+// own butterfly's 16 outputs again.  Operands are in the canonical K-major
+// layout without swizzle: 8-row x 16-byte core matrices, 128 B apart along K
+// (leading byte offset) and 512 B apart along M/N (stride byte offset).
+// ---------------------------------------------------------------------------
+struct TcCtx {
+    uint32_t tmem = 0;   // TMEM base address of the accumulators
+    uint32_t phase = 0;  // parity of the next MMA-completion phase
+    unsigned char* a = nullptr;
+    unsigned char* b = nullptr;
+    uint64_t* bar = nullptr;
+    float* red = nullptr;  // per-warp slots for the per-signal maximum
+    int* err = nullptr;
+    uint64_t wait_ns = 0;
+    bool dead = false;   // a bounded wait gave up: stop waiting, finish
+};
+
+__device__ __forceinline__ uint64_t umma_smem_desc(uint32_t saddr) {
+    uint64_t d = (uint64_t)((saddr & 0x3FFFF) >> 4);  // start address
+    d |= (uint64_t)(128 >> 4) << 16;                    // leading byte offset: next core matrix along K
+    d |= (uint64_t)(512 >> 4) << 32;                    // stride byte offset: next 8-row group
+    d |= (uint64_t)1 << 46;                             // descriptor version
+    return d;                                           // layout 0: no swizzle
+}
+
+template <int TC>
+__device__ __forceinline__ uint32_t umma_idesc() {
+    constexpr uint32_t fmt = TC == 2 ? 1u : 0u;  // operand type: 0 FP16, 1 BF16
+    return (1u << 4)               // accumulate in FP32
+           | (fmt << 7) | (fmt << 10)  // A and B type (same type for both)
+           | ((32u >> 3) << 17)    // N = 32
+           | ((128u >> 4) << 24);  // M = 128; A and B K-major, no negation
+}
+
+template <int TC>
+__device__ __forceinline__ uint32_t pack2(float lo, float hi) {
+    if constexpr (TC == 2) {
+        __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+        return *reinterpret_cast<uint32_t*>(&h);
+    } else {
+        __half2 h = __floats2half2_rn(lo, hi);
+        return *reinterpret_cast<uint32_t*>(&h);
+    }
+}
+
+template <int TC>
+__device__ __forceinline__ uint16_t to_bits(float x) {
+    if constexpr (TC == 2) {
+        return __bfloat16_as_ushort(__float2bfloat16_rn(x));
+    } else {
+        return __half_as_ushort(__float2half_rn(x));
+    }
+}
+
+// cos and sin of 2 pi m / 16 from the butterfly constants
+__device__ __forceinline__ float2 cs16(int m) {
+    const float c[5] = {1.0f, kCos8, kSqrtHalf, kSin8, 0.0f};  // cos(2 pi k/16), k = 0..4
+    m &= 15;
+    const int q = m >> 2, k = m & 3;  // angle = q * pi/2 + k * pi/8
+    float cc = c[k], ss = c[4 - k];   // cos, sin of k * pi/8
+    switch (q) {
+        case 0: return make_float2(cc, ss);
+        case 1: return make_float2(-ss, cc);
+        case 2: return make_float2(-cc, -ss);
+        default: return make_float2(ss, -cc);
+    }
+}
+
+template <class C>
+__device__ __forceinline__ void tc_setup(TcCtx& tc, unsigned char* base, int* err, uint64_t wait_ns) {
+    tc.a = base;
+    tc.b = base + C::kTcTiles * 8192;
+    tc.bar = reinterpret_cast<uint64_t*>(tc.b + 2048);
+    uint32_t* slot = reinterpret_cast<uint32_t*>(tc.b + 2048 + 8);
+    tc.red = reinterpret_cast<float*>(tc.b + 2048 + 64);
+    tc.err = err;
+    tc.wait_ns = wait_ns;
+    if ((threadIdx.x >> 5) == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)),
+                     "r"(C::kTcCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (threadIdx.x == 0) {
+        mbar_init(tc.bar, 1);
+        fence_mbar_init();
+    }
+    // B = real form of F, N x K (K-major)
+    for (int i = threadIdx.x; i < 32 * 32; i += C::NT) {
+        const int n = i >> 5, k = i & 31;
+        const int q = n & 15, r = k & 15;
+        const float2 w = cs16(q * r);
+        float val;
+        if (n < 16) val = k < 16 ? w.x : w.y;  // Re y: c, s
+        else val = k < 16 ? -w.y : w.x;        // Im y: -s, c
+        *reinterpret_cast<uint16_t*>(tc.b + (n >> 3) * 512 + (k >> 3) * 128 + (n & 7) * 16 + (k & 7) * 2) =
+            to_bits<C::TC>(val);
+    }
+    fence_proxy_async_smem();
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    tc.tmem = *slot;
+}
+
+template <class C>
+__device__ __forceinline__ void tc_teardown(TcCtx& tc) {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if ((threadIdx.x >> 5) == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tc.tmem), "r"(C::kTcCols)
+                     : "memory");
+    }
+}
+
+// Every thread of the block calls this with its own butterfly's 16 inputs.
+template <class C>
+__device__ __forceinline__ void tc_dft16(float2* v, TcCtx& tc) {
+    const int tid = threadIdx.x;
+    const int row = tid & 127;
+    unsigned char* arow = tc.a + (tid >> 7) * 8192 + (row >> 3) * 512 + (row & 7) * 16;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {  // K chunk c: Re x_0..7, Re x_8..15, Im x_0..7, Im x_8..15
+        const int o = (c & 1) * 8;
+        uint4 q;
+        if (c < 2) {
+            q.x = pack2<C::TC>(v[o + 0].x, v[o + 1].x);
+            q.y = pack2<C::TC>(v[o + 2].x, v[o + 3].x);
+            q.z = pack2<C::TC>(v[o + 4].x, v[o + 5].x);
+            q.w = pack2<C::TC>(v[o + 6].x, v[o + 7].x);
+        } else {
+            q.x = pack2<C::TC>(v[o + 0].y, v[o + 1].y);
+            q.y = pack2<C::TC>(v[o + 2].y, v[o + 3].y);
+            q.z = pack2<C::TC>(v[o + 4].y, v[o + 5].y);
+            q.w = pack2<C::TC>(v[o + 6].y, v[o + 7].y);
+        }
+        *reinterpret_cast<uint4*>(arow + c * 128) = q;
+    }
+    fence_proxy_async_smem();  // make the rows visible to the tensor core
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (tid == 0) {
+        const uint32_t idesc = umma_idesc<C::TC>();
+        const uint32_t a0 = smem_u32(tc.a), b0 = smem_u32(tc.b);
+#pragma unroll
+        for (int t = 0; t < C::kTcTiles; ++t) {
+#pragma unroll
+            for (int ks = 0; ks < 2; ++ks) {
+                const uint64_t da = umma_smem_desc(a0 + t * 8192 + ks * 256);
+                const uint64_t db = umma_smem_desc(b0 + ks * 256);
+                asm volatile(
+                    "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tc.tmem + 32 * t),
+                    "l"(da), "l"(db), "r"(idesc), "r"(ks)
+                    : "memory");
+            }
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         smem_u32(tc.bar))
+                     : "memory");
+    }
+    if (!tc.dead && !mbar_wait_bounded(tc.bar, tc.phase, tc.wait_ns)) {
+        tc.dead = true;
+        atomicCAS(tc.err, 0, kErrTimeout);
+    }
+    tc.phase ^= 1;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const int warp = tid >> 5;
+    const uint32_t taddr = tc.tmem + ((uint32_t)((warp & 3) * 32) << 16) + 32 * (warp >> 2);
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int q = 0; q < 16; ++q) v[q] = make_float2(__uint_as_float(r[q]), __uint_as_float(r[16 + q]));
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+
+// Per-signal power-of-two prescale for the tensor-core path: returns e with
+// max(|Re|, |Im|) * 2^-e < 1 over the signal (0 for an all-zero signal).
+template <class C>
+__device__ __forceinline__ int tc_signal_exponent(const float2 (&v)[C::E], TcCtx& tc) {
+    float m = 0.0f;
+#pragma unroll
+    for (int i = 0; i < C::E; ++i) m = fmaxf(m, fmaxf(fabsf(v[i].x), fabsf(v[i].y)));
+    if constexpr (C::T <= 32) {
+#pragma unroll
+        for (int o = 1; o < C::T; o <<= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    } else {
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        const int warp = threadIdx.x >> 5;
+        if ((threadIdx.x & 31) == 0) tc.red[warp] = m;
+        __syncthreads();
+        constexpr int W = C::T / 32;
+        const int w0 = (warp / W) * W;
+        m = 0.0f;
+#pragma unroll
+        for (int w = 0; w < W; ++w) m = fmaxf(m, tc.red[w0 + w]);
+    }
+    int e = 0;
+    frexpf(m, &e);
+    return m > 0.0f ? e : 0;
+}
 
 // Butterfly handled by thread t in slot c of stage s.  The first and the last
 // stage give a thread neighbouring butterflies (vectorised HBM access); the
@@ -320,7 +551,7 @@ __device__ __forceinline__ int bfly(int t, int c) {
 }
 
 template <class C, int s>
-__device__ __forceinline__ void twist_and_dft(float2 (&v)[C::E], int t, const float2* __restrict__ tw) {
+__device__ __forceinline__ void twist_and_dft(float2 (&v)[C::E], int t, const float2* __restrict__ tw, TcCtx& tc) {
     constexpr int R = C::radix(s);
     constexpr int K = C::E / R;
     constexpr int Ns = C::ns(s);
@@ -332,7 +563,11 @@ __device__ __forceinline__ void twist_and_dft(float2 (&v)[C::E], int t, const fl
 #pragma unroll
             for (int r = 1; r < R; ++r) v[c * R + r] = cmul(v[c * R + r], __ldg(twp + (r - 1) * Ns));
         }
-        Dft<R>::run(&v[c * R]);
+        if constexpr (C::TC != 0 && R == 16 && K == 1) {
+            tc_dft16<C>(&v[0], tc);
+        } else {
+            Dft<R>::run(&v[c * R]);
+        }
     }
 }
 
@@ -429,7 +664,7 @@ __device__ __forceinline__ void exchange_barrier() {
 // stages 1..M-1: exchange through shared memory, then butterflies
 template <class C, int s>
 __device__ __forceinline__ void rest_stages(float2 (&v)[C::E], float2* smem, int& buf, int sb, int t,
-                                            const float2* __restrict__ tw) {
+                                            const float2* __restrict__ tw, TcCtx& tc) {
     if constexpr (s < C::M) {
         float2* b = smem + buf * (C::S * C::N);
         if constexpr (C::kWarpLocal) __syncwarp();  // previous readers of b are done
@@ -437,8 +672,8 @@ __device__ __forceinline__ void rest_stages(float2 (&v)[C::E], float2* smem, int
         exchange_barrier<C>();
         gather<C, s>(v, b, sb, t);
         if constexpr (C::kBuffers == 2) buf ^= 1;
-        twist_and_dft<C, s>(v, t, tw);
-        rest_stages<C, s + 1>(v, smem, buf, sb, t, tw);
+        twist_and_dft<C, s>(v, t, tw, tc);
+        rest_stages<C, s + 1>(v, smem, buf, sb, t, tw, tc);
     }
 }
 
@@ -447,14 +682,14 @@ template <class C, bool INV>
 __global__ void __launch_bounds__(C::NT, C::MINB)
     fft_stockham_kernel(const float2* in, float2* out, int64_t batch, const float2* __restrict__ tw, float scale,
                         int* err, uint64_t wait_ns) {
-    (void)err;
-    (void)wait_ns;
     extern __shared__ __align__(16) float2 smem[];
     const int tid = threadIdx.x;
     const int sl = tid / C::T;
     const int t = tid % C::T;
     const int sb = sl * C::N;
     const int64_t ntiles = (batch + C::S - 1) / C::S;
+    TcCtx tc;
+    if constexpr (C::TC != 0) tc_setup<C>(tc, reinterpret_cast<unsigned char*>(smem) + C::kTcOffset, err, wait_ns);
     int buf = 0;
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int64_t sig = tile * C::S + sl;
@@ -462,10 +697,19 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
         const int64_t base = sig * C::N;
         float2 v[C::E];
         load_first<C, INV>(v, in + base, t, active);
-        twist_and_dft<C, 0>(v, t, tw);
-        rest_stages<C, 1>(v, smem, buf, sb, t, tw);
-        store_last<C, INV>(v, out + base, t, active, scale);
+        float sc = scale;
+        if constexpr (C::TC != 0) {
+            const int e = tc_signal_exponent<C>(v, tc);
+            const float f = ldexpf(1.0f, -e);
+#pragma unroll
+            for (int i = 0; i < C::E; ++i) v[i] = make_float2(v[i].x * f, v[i].y * f);
+            sc = ldexpf(scale, e);
+        }
+        twist_and_dft<C, 0>(v, t, tw, tc);
+        rest_stages<C, 1>(v, smem, buf, sb, t, tw, tc);
+        store_last<C, INV>(v, out + base, t, active && !tc.dead, sc);
     }
+    if constexpr (C::TC != 0) tc_teardown<C>(tc);
 }
 
 // stage-0 inputs from a dense tile in shared memory (the bulk-copy ring)
@@ -524,6 +768,8 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
             if (tile < ntiles) issue(d, tile);
         }
     }
+    TcCtx tc;
+    if constexpr (C::TC != 0) tc_setup<C>(tc, reinterpret_cast<unsigned char*>(smem) + C::kTcOffset, err, wait_ns);
     bool dead = false;
     int buf = 0;
     int64_t it = 0;
@@ -535,10 +781,17 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
             atomicCAS(err, 0, kErrTimeout);
         }
         const int64_t sig = tile * C::S + sl;
-        const bool active = sig < batch && !dead;
         float2 v[C::E];
         gather_tile<C, INV>(v, ring + slot * TILE, sb, t);
-        twist_and_dft<C, 0>(v, t, tw);
+        float sc = scale;
+        if constexpr (C::TC != 0) {
+            const int e = tc_signal_exponent<C>(v, tc);
+            const float f = ldexpf(1.0f, -e);
+#pragma unroll
+            for (int i = 0; i < C::E; ++i) v[i] = make_float2(v[i].x * f, v[i].y * f);
+            sc = ldexpf(scale, e);
+        }
+        twist_and_dft<C, 0>(v, t, tw, tc);
         float2* b = smem + buf * TILE;
         scatter<C, 0>(v, b, sb, t);
         __syncthreads();  // every thread is done with ring[slot]
@@ -551,10 +804,12 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
         }
         gather<C, 1>(v, b, sb, t);
         buf ^= 1;
-        twist_and_dft<C, 1>(v, t, tw);
-        rest_stages<C, 2>(v, smem, buf, sb, t, tw);
-        store_last<C, INV>(v, out + sig * C::N, t, active, scale);
+        twist_and_dft<C, 1>(v, t, tw, tc);
+        rest_stages<C, 2>(v, smem, buf, sb, t, tw, tc);
+        const bool active = sig < batch && !dead && !tc.dead;
+        store_last<C, INV>(v, out + sig * C::N, t, active, sc);
     }
+    if constexpr (C::TC != 0) tc_teardown<C>(tc);
 }
 
 // ---------------------------------------------------------------------------

@@ -28,7 +28,7 @@ static void fill_generic_twiddles(float* host) {
     }
 }
 
-static void fill_nothing(float*) {}
+[[maybe_unused]] static void fill_nothing(float*) {}
 
 template <class C>
 static KernelEntry generic_entry(int variant) {
@@ -44,6 +44,8 @@ static KernelEntry generic_entry(int variant) {
     for (int s = 0; s < 4; ++s) e.radix[s] = C::radix(s);
     e.min_blocks = C::MINB;
     e.pipeline = C::PIPE;
+    e.tc = C::TC;
+    e.tmem_cols = C::TC ? C::kTcCols : 0;
     e.twiddles = C::kTwiddles;
     if constexpr (C::PIPE > 0) {
         e.kernel_fwd = reinterpret_cast<const void*>(&fft_stockham_ring_kernel<C, false>);
@@ -71,6 +73,8 @@ static KernelEntry small_entry(int variant) {
     e.radix[0] = SC::N;
     e.min_blocks = 1;
     e.pipeline = 0;
+    e.tc = 0;
+    e.tmem_cols = 0;
     e.twiddles = 0;
     e.kernel_fwd = reinterpret_cast<const void*>(&fft_small_kernel<SC, false>);
     e.kernel_inv = reinterpret_cast<const void*>(&fft_small_kernel<SC, true>);
@@ -150,8 +154,8 @@ int GBFFT_ENTRIES_FN(GBFFT_LOG2N)(gbfft::KernelEntry* out, int max) {
             if (e.variant + 1 > count) count = e.variant + 1;
         }
     };
-#define GBFFT_GX(L, V, E, S, R0, R1, R2, R3, MINB, PIPE) \
-    GBFFT_ONLY_##L(put(generic_entry<Cfg<L, E, S, R0, R1, R2, R3, MINB, PIPE>>(V));)
+#define GBFFT_GX(L, V, E, S, R0, R1, R2, R3, MINB, PIPE, TC) \
+    GBFFT_ONLY_##L(put(generic_entry<Cfg<L, E, S, R0, R1, R2, R3, MINB, PIPE, TC>>(V));)
     GBFFT_GENERIC_SCHEDULES(GBFFT_GX)
 #undef GBFFT_GX
 #define GBFFT_SX(L, V, W) GBFFT_ONLY_##L(put(small_entry<SmallCfg<L, W>>(V));)

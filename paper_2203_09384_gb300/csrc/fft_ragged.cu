@@ -110,10 +110,11 @@ __device__ __forceinline__ void ragged_tile(const RaggedArgs& a, const RaggedIte
     const float2* tw = a.tw + a.tw_off[C::LOG2N];
     const float scale = a.scale_mode ? 1.0f / (float)C::N : 1.0f;
     int buf = 0;
+    TcCtx tc;  // FP32 butterflies only
     float2 v[C::E];
     load_first<C, INV>(v, a.in + off, t, active);
-    twist_and_dft<C, 0>(v, t, tw);
-    rest_stages<C, 1>(v, smem, buf, sl * C::N, t, tw);
+    twist_and_dft<C, 0>(v, t, tw, tc);
+    rest_stages<C, 1>(v, smem, buf, sl * C::N, t, tw, tc);
     store_last<C, INV>(v, a.out + off, t, active, scale);
 }
 

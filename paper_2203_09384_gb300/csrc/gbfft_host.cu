@@ -163,7 +163,6 @@ fft_status_t fft_validate(int64_t n, int64_t batch, int direction, int dtype, ui
     if (direction != FFT_FORWARD && direction != FFT_INVERSE) return FFT_ERR_INVALID_VALUE;
     if (dtype != FFT_C64 && dtype != FFT_C64_TC_F16 && dtype != FFT_C64_TC_BF16) return FFT_ERR_INVALID_VALUE;
     if (flags & ~kKnownFlags) return FFT_ERR_INVALID_VALUE;
-    if (dtype != FFT_C64) return FFT_ERR_UNSUPPORTED;
     return FFT_OK;
 }
 
@@ -189,9 +188,22 @@ fft_status_t fft_plan_create_ex(int64_t n, int64_t batch, int direction, int dty
 
     const int log2n = ilog2(n);
     LengthVariants* lv = &registry()[log2n];
+    const int want_tc = dtype == FFT_C64_TC_F16 ? 1 : dtype == FFT_C64_TC_BF16 ? 2 : 0;
     int variant = (int)((flags & FFT_FLAG_VARIANT_MASK) >> 8) - 1;
-    if (variant < 0) variant = lv->preferred.load();
+    if (variant < 0) {
+        // FP32: the length's default.  Tensor-core types: the first variant of
+        // that type; lengths without a radix-16 tensor-core schedule run FP32.
+        variant = lv->preferred.load();
+        if (want_tc) {
+            for (int v = 0; v < lv->count; ++v)
+                if (lv->v[v].kernel_fwd && lv->v[v].tc == want_tc) {
+                    variant = v;
+                    break;
+                }
+        }
+    }
     if (variant >= lv->count || !lv->v[variant].kernel_fwd) return FFT_ERR_INVALID_VALUE;
+    if (lv->v[variant].tc != 0 && lv->v[variant].tc != want_tc) return FFT_ERR_INVALID_VALUE;
     const KernelEntry* e = &lv->v[variant];
     gbfft_plan* p = new (std::nothrow) gbfft_plan();
     if (!p) return FFT_ERR_ALLOC;
@@ -261,6 +273,16 @@ fft_status_t fft_plan_create_ex(int64_t n, int64_t batch, int direction, int dty
         return FFT_ERR_CUDA;
     }
     const int64_t tiles = (batch + e->signals_per_block - 1) / e->signals_per_block;
+    if (e->tmem_cols > 0 && per_sm * e->tmem_cols > 512) {
+        // every resident block holds its TMEM columns for its whole life; more
+        // than 512 per SM would leave a block waiting for columns forever
+        per_sm = 512 / e->tmem_cols;
+        if (per_sm < 1) {
+            cudaFree(dmem);
+            delete p;
+            return FFT_ERR_UNSUPPORTED;
+        }
+    }
     const int64_t resident = (int64_t)sms * per_sm;
     p->grid = tiles < resident ? tiles : resident;
     *plan = p;
@@ -395,6 +417,7 @@ fft_status_t fft_plan_get_info(fft_plan_t p, fft_plan_info_t* info) {
     info->pipeline = e->pipeline;
     info->min_blocks = e->min_blocks;
     info->kernel_kind = (int)e->kind;
+    info->tc = e->tc;
     for (int s = 0; s < e->num_stages && s < 4; ++s) info->radix[s] = e->radix[s];
     info->grid = p->grid;
     info->smem_bytes = e->smem_bytes;
@@ -410,9 +433,18 @@ int fft_variant_count(int64_t n) {
 fft_status_t fft_set_default_variant(int64_t n, int variant) {
     if (n < 2 || n > 2048 || (n & (n - 1)) != 0) return FFT_ERR_INVALID_SIZE;
     LengthVariants* lv = &registry()[ilog2(n)];
-    if (variant < 0 || variant >= lv->count || !lv->v[variant].kernel_fwd) return FFT_ERR_INVALID_VALUE;
+    if (variant < 0 || variant >= lv->count || !lv->v[variant].kernel_fwd || lv->v[variant].tc != 0)
+        return FFT_ERR_INVALID_VALUE;
     lv->preferred.store(variant);
     return FFT_OK;
+}
+
+int fft_variant_dtype(int64_t n, int variant) {
+    if (n < 2 || n > 2048 || (n & (n - 1)) != 0) return -1;
+    LengthVariants* lv = &registry()[ilog2(n)];
+    if (variant < 0 || variant >= lv->count || !lv->v[variant].kernel_fwd) return -1;
+    const int tc = lv->v[variant].tc;
+    return tc == 1 ? FFT_C64_TC_F16 : tc == 2 ? FFT_C64_TC_BF16 : FFT_C64;
 }
 
 int fft_get_default_variant(int64_t n) {

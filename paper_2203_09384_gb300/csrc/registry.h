@@ -25,6 +25,8 @@ struct KernelEntry {
     int radix[4];
     int min_blocks;          // launch-bounds hint
     int pipeline;            // bulk-copy ring depth (0 = none)
+    int tc;                  // 0 FP32, 1 FP16 / 2 BF16 tensor-core radix-16 stages
+    int tmem_cols;           // TMEM columns one block allocates (tensor-core variants)
     int twiddles;            // complex64 entries in the twiddle table
     const void* kernel_fwd;
     const void* kernel_inv;

@@ -75,18 +75,18 @@ def ragged_uniform(lengths: torch.Tensor, seed: int) -> torch.Tensor:
     return uniform(1, total, seed).reshape(total)
 
 
-def scaled_normal(batch: int, n: int, seed: int, lo: float = -3.0, hi: float = 3.0):
+def scaled_normal(batch: int, n: int, seed: int, lo: float = -3.0, hi: float = 3.0, device="cpu"):
     """complex64 [batch, n]: N(0,1) signals, signal i scaled by 10^u_i, u_i ~ U(lo, hi).
 
     The signal values are drawn first, then the exponents, from one generator.
-    Returns (x, scale) with scale a float64 tensor [batch].
+    Returns (x, scale) with scale a float64 tensor [batch] (on the CPU).
     """
-    g = _gen(seed)
-    x = normal(batch, n, seed, generator=g)
-    u = torch.rand(batch, generator=g, dtype=torch.float64) * (hi - lo) + lo
-    s = torch.pow(torch.tensor(10.0, dtype=torch.float64), u)
-    xs = (x.to(torch.complex128) * s[:, None]).to(torch.complex64)
-    return xs, s
+    g = _gen(seed, device)
+    x = normal(batch, n, seed, device=device, generator=g)
+    u = torch.rand(batch, generator=g, dtype=torch.float64, device=device) * (hi - lo) + lo
+    s = torch.pow(torch.tensor(10.0, dtype=torch.float64, device=device), u)
+    xs = torch.view_as_complex(torch.view_as_real(x) * s.to(torch.float32)[:, None, None])
+    return xs, s.cpu()
 
 
 def delta(n: int, pos: int = 0, batch: int = 1) -> torch.Tensor:

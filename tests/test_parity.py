@@ -59,7 +59,8 @@ def _batch_for(n):
 
 
 def _variants():
-    return [(n, v) for n in POW2 for v in range(gb.fft_variant_count(n))]
+    return [(n, v) for n in POW2 for v in range(gb.fft_variant_count(n))
+            if gb.fft_variant_dtype(n, v) == gb.FFT_C64]
 
 
 @pytest.mark.parametrize("n,variant", _variants())
@@ -197,9 +198,13 @@ def test_variant_selection():
         count = gb.fft_variant_count(n)
         assert count >= 1
         for v in range(count):
-            p = gb.Plan(n, 64, variant=v)
+            dt = gb.DTYPE_NAMES[gb.fft_variant_dtype(n, v)]
+            p = gb.Plan(n, 64, variant=v, dtype=dt)
             assert p.info().variant == v
             p.close()
+            if dt != "c64":  # a tensor-core variant is refused for FP32 plans
+                with pytest.raises(gb.FFTError):
+                    gb.Plan(n, 64, variant=v)
         with pytest.raises(gb.FFTError):
             gb.Plan(n, 64, variant=count)
     assert gb.fft_variant_count(12) == 0

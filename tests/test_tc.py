@@ -1,0 +1,88 @@
+"""FP16 / BF16 tensor-core radix-16 stages (tcgen05) against the FP64 oracle.
+
+Workload: complex N(0,1) signals, each scaled by 10^u with u ~ U(-3, 3)
+(seed 4), so that a fixed FP16 range would overflow or underflow without the
+per-signal power-of-two prescale.  Bar: per-signal relative L2 <= 5e-3.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from tests.helpers import max_rel_l2, rel_l2_per_signal, to_np
+
+pytestmark = pytest.mark.gpu
+
+import paper_2203_09384_gb300 as gb  # noqa: E402
+
+TC_TOL = 5e-3
+TC_LENGTHS = [128, 256, 1024, 2048]
+
+
+def run(x, n, dtype, inverse=False):
+    plan = gb.Plan(n, x.shape[0], inverse=inverse, dtype=dtype)
+    out = plan.execute(x)
+    torch.cuda.synchronize()
+    assert plan.error() == 0
+    info = plan.info()
+    plan.close()
+    return out, info
+
+
+@pytest.mark.parametrize("dtype", ["tc_f16", "tc_bf16"])
+@pytest.mark.parametrize("n", TC_LENGTHS)
+@pytest.mark.parametrize("inverse", [False, True])
+def test_tc_against_oracle(n, dtype, inverse):
+    batch = 3 * 152 + 7
+    x, _ = synth.scaled_normal(batch, n, seed=4)
+    out, info = run(x.cuda(), n, dtype, inverse)
+    assert info.tc == (1 if dtype == "tc_f16" else 2)
+    err = rel_l2_per_signal(to_np(out), oracle.reference(x.numpy(), inverse, threads=8))
+    assert err.max() <= TC_TOL, (n, dtype, err.max())
+
+
+@pytest.mark.parametrize("dtype", ["tc_f16", "tc_bf16"])
+@pytest.mark.parametrize("n", [256, 2048])
+def test_precision_workload_sample(n, dtype):
+    """N in {256, 2048}, batch 2^17, as the benchmark runs it; a seeded sample
+    of signals (first, last, random) against the oracle."""
+    batch = 2 ** 17
+    x, _ = synth.scaled_normal(batch, n, seed=4, device="cuda")
+    out, _ = run(x, n, dtype)
+    rng = np.random.default_rng(n)
+    idx = torch.from_numpy(np.unique(np.concatenate([[0, batch - 1], rng.integers(0, batch, 254)]))).cuda()
+    want = oracle.reference(x.index_select(0, idx).cpu().numpy(), threads=8)
+    assert max_rel_l2(to_np(out.index_select(0, idx)), want) <= TC_TOL
+
+
+@pytest.mark.parametrize("dtype", ["tc_f16", "tc_bf16"])
+def test_tc_exact_cases(dtype):
+    """Inputs whose products are exact in FP16/BF16: delta -> all ones; the
+    prescale is a power of two, so huge and tiny deltas come out exact too."""
+    for n in TC_LENGTHS:
+        for amp in (1.0, 2.0 ** 40, 2.0 ** -40):
+            d = synth.delta(n, 0, batch=3) * amp
+            out, _ = run(d.cuda(), n, dtype)
+            assert torch.equal(out.cpu(), torch.full((3, n), amp, dtype=torch.complex64))
+        z = torch.zeros(2, n, dtype=torch.complex64)
+        out, _ = run(z.cuda(), n, dtype)
+        assert torch.count_nonzero(out) == 0
+
+
+def test_lengths_without_radix16_stage_run_fp32():
+    x = synth.uniform(40, 64, seed=2)
+    out, info = run(x.cuda(), 64, "tc_f16")
+    assert info.tc == 0
+    assert max_rel_l2(to_np(out), oracle.reference(x.numpy())) <= 1e-5
+
+
+def test_tc_accuracy_is_reported_not_hidden():
+    """FP16 must beat BF16 by a wide margin on the same data (2^-11 vs 2^-8
+    operand rounding); both stay under the 5e-3 bar."""
+    x, _ = synth.scaled_normal(512, 256, seed=4)
+    want = oracle.reference(x.numpy(), threads=8)
+    e16 = max_rel_l2(to_np(run(x.cuda(), 256, "tc_f16")[0]), want)
+    e_bf = max_rel_l2(to_np(run(x.cuda(), 256, "tc_bf16")[0]), want)
+    e32 = max_rel_l2(to_np(run(x.cuda(), 256, "c64")[0]), want)
+    assert e32 < 1e-6 < e16 < e_bf <= TC_TOL, (e32, e16, e_bf)
