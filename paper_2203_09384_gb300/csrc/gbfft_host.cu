@@ -64,6 +64,32 @@ int ilog2(int64_t n) {
     return l;
 }
 
+// Resident blocks per SM from registers, shared memory and threads alone.
+// The occupancy API returns 1 for every kernel that allocates tensor memory
+// (TMEM); measured on GB300, such kernels do run several blocks per SM, so
+// for them the limit is worked out here and then capped by TMEM capacity.
+int occupancy_without_tmem(const void* kernel, int threads, int smem_bytes, int dev) {
+    cudaFuncAttributes fa;
+    int regs_sm = 0, smem_sm = 0, thr_sm = 0, blk_sm = 0, smem_reserved = 0;
+    if (cudaFuncGetAttributes(&fa, kernel) != cudaSuccess ||
+        cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&thr_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&blk_sm, cudaDevAttrMaxBlocksPerMultiprocessor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&smem_reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    const int warps = (threads + 31) / 32;
+    const int regs_warp = ((fa.numRegs * 32 + 255) / 256) * 256;  // allocated per warp in 256-register units
+    int by_regs = regs_warp > 0 ? regs_sm / (regs_warp * warps) : blk_sm;
+    int by_smem = smem_sm / ((int)fa.sharedSizeBytes + smem_bytes + smem_reserved);
+    int by_thr = thr_sm / threads;
+    int n = by_regs < by_smem ? by_regs : by_smem;
+    n = n < by_thr ? n : by_thr;
+    return n < blk_sm ? n : blk_sm;
+}
+
 constexpr uint32_t kKnownFlags = FFT_FLAG_UNNORMALIZED | FFT_FLAG_SCALE_FORWARD | FFT_FLAG_VARIANT_MASK;
 constexpr uint64_t kDefaultWaitNs = 4000000000ull;  // bounded device waits: 4 s
 
@@ -273,15 +299,16 @@ fft_status_t fft_plan_create_ex(int64_t n, int64_t batch, int direction, int dty
         return FFT_ERR_CUDA;
     }
     const int64_t tiles = (batch + e->signals_per_block - 1) / e->signals_per_block;
+    if (e->tmem_cols > 0) per_sm = occupancy_without_tmem(p->kernel, e->threads_per_block, e->smem_bytes, dev);
     if (e->tmem_cols > 0 && per_sm * e->tmem_cols > 512) {
         // every resident block holds its TMEM columns for its whole life; more
         // than 512 per SM would leave a block waiting for columns forever
         per_sm = 512 / e->tmem_cols;
-        if (per_sm < 1) {
-            cudaFree(dmem);
-            delete p;
-            return FFT_ERR_UNSUPPORTED;
-        }
+    }
+    if (per_sm < 1) {
+        cudaFree(dmem);
+        delete p;
+        return FFT_ERR_UNSUPPORTED;
     }
     const int64_t resident = (int64_t)sms * per_sm;
     p->grid = tiles < resident ? tiles : resident;
