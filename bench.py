@@ -330,6 +330,23 @@ def run_reference(args):
     return 0
 
 
+def reduce_max_over_ranks(ms: float, device=None) -> float:
+    """The slowest rank's time (the job is done when every rank is done)."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return ms
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_gbs(bytes_per_rank: float, world: int, ms: float) -> float:
+    """Aggregate rate: the bytes every rank moved over the slowest rank's time."""
+    return bytes_per_rank * world / (ms * 1e-3) / 1e9
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -389,10 +406,7 @@ def run_ours(args):
     ms = t_start.elapsed_time(t_end)
     per_launch = {k: [ev[s][i][0].elapsed_time(ev[s][i][1]) for s in range(args.steps)]
                   for i, k in enumerate(LOG2NS)}
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = reduce_max_over_ranks(ms, dev)
     # correctness spot check of the timed output (last length) before reporting
     assert all(p.error() == 0 for p in plans.values())
 
@@ -432,7 +446,7 @@ def run_ours(args):
 
     step_bytes = BYTES_PER_ELEM * ELEMS * len(LOG2NS)
     ms_per_step = ms / args.steps
-    value = step_bytes * world / (ms_per_step * 1e-3) / 1e9
+    value = whole_job_gbs(step_bytes, world, ms_per_step)
     peak, peak_src = peaks()
     per_n = {}
     for k in LOG2NS:

@@ -63,7 +63,13 @@ enum {
     FFT_FLAG_SCALE_FORWARD = 1u << 1,
     /* Bits 8..11: 1 + the schedule variant to use (0 = the length's default,
      * see fft_set_default_variant).  Build them with FFT_FLAG_VARIANT(k). */
-    FFT_FLAG_VARIANT_MASK = 0xFu << 8
+    FFT_FLAG_VARIANT_MASK = 0xFu << 8,
+    /* Test hook for failure detection: kernels with device-side waits (the
+     * bulk-copy ring, the tensor-core stages) issue nothing, so their bounded
+     * waits run out after the plan's wait limit and fft_plan_get_error
+     * reports FFT_ERR_TIMEOUT.  The output is not written.  Plans of kernels
+     * without device-side waits ignore it. */
+    FFT_FLAG_TEST_STALL = 1u << 16
 };
 #define FFT_FLAG_VARIANT(k) ((uint32_t)((k) + 1) << 8)
 

@@ -23,6 +23,7 @@ from ._abi import (FFT_C64, FFT_C64_TC_BF16, FFT_C64_TC_F16, FFT_FLAG_SCALE_FORW
                    fft_set_default_variant, fft_variant_count,
                    FFT_FORWARD, FFT_INVERSE, FFTError, STATUS, fft_execute, fft_plan_create,
                    fft_plan_create_ex, fft_plan_destroy, fft_plan_get_error, fft_plan_get_info,
+                   fft_plan_set_wait_limit, FFT_FLAG_TEST_STALL,
                    fft_validate, lib)
 
 __all__ = ["Plan", "RaggedPlan", "fft", "ifft", "FFTFunction", "IFFTFunction", "fft_plan_create",
@@ -42,7 +43,7 @@ class Plan:
 
     def __init__(self, n: int, batch: int, inverse: bool = False, dtype: str = "c64",
                  normalized: bool = True, device=None, scale_forward: bool = False,
-                 variant: int | None = None):
+                 variant: int | None = None, extra_flags: int = 0):
         self.n, self.batch, self.inverse = int(n), int(batch), bool(inverse)
         self.dtype = dtype
         self.normalized = normalized
@@ -53,6 +54,7 @@ class Plan:
             flags |= FFT_FLAG_SCALE_FORWARD
         if variant is not None:
             flags |= FFT_FLAG_VARIANT(variant)
+        flags |= int(extra_flags)
         direction = FFT_INVERSE if inverse else FFT_FORWARD
         self.handle = None
         with torch.cuda.device(self.device):
@@ -79,6 +81,9 @@ class Plan:
 
     def error(self) -> int:
         return fft_plan_get_error(self.handle)
+
+    def set_wait_limit(self, nanoseconds: int) -> None:
+        fft_plan_set_wait_limit(self.handle, nanoseconds)
 
     def close(self):
         if self.handle:

@@ -21,6 +21,7 @@ FFT_C64_TC_BF16 = 2
 FFT_FLAG_UNNORMALIZED = 1 << 0
 FFT_FLAG_SCALE_FORWARD = 1 << 1
 FFT_FLAG_VARIANT_MASK = 0xF << 8
+FFT_FLAG_TEST_STALL = 1 << 16
 
 
 def FFT_FLAG_VARIANT(k: int) -> int:

@@ -338,6 +338,7 @@ struct TcCtx {
     int* err = nullptr;
     uint64_t wait_ns = 0;
     bool dead = false;   // a bounded wait gave up: stop waiting, finish
+    bool stall = false;  // failure-detection test mode: issue no MMA
 };
 
 __device__ __forceinline__ uint64_t umma_smem_desc(uint32_t saddr) {
@@ -466,7 +467,7 @@ __device__ __forceinline__ void tc_dft16(float2* v, TcCtx& tc) {
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (tid == 0) {
+    if (tid == 0 && !tc.stall) {
         const uint32_t idesc = umma_idesc<C::TC>();
         const uint32_t a0 = smem_u32(tc.a), b0 = smem_u32(tc.b);
 #pragma unroll
@@ -681,7 +682,7 @@ __device__ __forceinline__ void rest_stages(float2 (&v)[C::E], float2* smem, int
 template <class C, bool INV>
 __global__ void __launch_bounds__(C::NT, C::MINB)
     fft_stockham_kernel(const float2* in, float2* out, int64_t batch, const float2* __restrict__ tw, float scale,
-                        int* err, uint64_t wait_ns) {
+                        int* err, uint64_t wait_ns, int stall) {
     extern __shared__ __align__(16) float2 smem[];
     const int tid = threadIdx.x;
     const int sl = tid / C::T;
@@ -690,6 +691,7 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
     const int64_t ntiles = (batch + C::S - 1) / C::S;
     TcCtx tc;
     if constexpr (C::TC != 0) tc_setup<C>(tc, reinterpret_cast<unsigned char*>(smem) + C::kTcOffset, err, wait_ns);
+    tc.stall = stall != 0;
     int buf = 0;
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int64_t sig = tile * C::S + sl;
@@ -738,7 +740,7 @@ __device__ __forceinline__ void gather_tile(float2 (&v)[C::E], const float2* til
 template <class C, bool INV>
 __global__ void __launch_bounds__(C::NT, C::MINB)
     fft_stockham_ring_kernel(const float2* in, float2* out, int64_t batch, const float2* __restrict__ tw,
-                             float scale, int* err, uint64_t wait_ns) {
+                             float scale, int* err, uint64_t wait_ns, int stall) {
     constexpr int D = C::PIPE;
     constexpr int TILE = C::S * C::N;
     extern __shared__ __align__(16) float2 smem[];
@@ -762,7 +764,9 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
         fence_mbar_init();
     }
     __syncthreads();
-    if (tid == 0) {
+    // stall != 0 is the failure-detection test mode: nothing is issued, so
+    // every wait below runs out, records FFT_ERR_TIMEOUT and the kernel ends
+    if (tid == 0 && !stall) {
         for (int d = 0; d < D; ++d) {
             const int64_t tile = blockIdx.x + (int64_t)d * gridDim.x;
             if (tile < ntiles) issue(d, tile);
@@ -770,7 +774,12 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
     }
     TcCtx tc;
     if constexpr (C::TC != 0) tc_setup<C>(tc, reinterpret_cast<unsigned char*>(smem) + C::kTcOffset, err, wait_ns);
+    tc.stall = stall != 0;
     bool dead = false;
+    if (stall) {  // wait for a phase nothing will complete: must give up after wait_ns
+        if (!mbar_wait_bounded(&bars[0], 0, wait_ns)) atomicCAS(err, 0, kErrTimeout);
+        dead = true;
+    }
     int buf = 0;
     int64_t it = 0;
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
@@ -795,7 +804,7 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
         float2* b = smem + buf * TILE;
         scatter<C, 0>(v, b, sb, t);
         __syncthreads();  // every thread is done with ring[slot]
-        if (tid == 0 && !dead) {
+        if (tid == 0 && !dead && !stall) {
             const int64_t next = tile + (int64_t)D * gridDim.x;
             if (next < ntiles) {
                 fence_proxy_async_smem();

@@ -198,7 +198,8 @@ extern "C" fft_status_t fft_execute_noalloc(int64_t n, int64_t batch, int direct
         ce = cudaLaunchKernel(kernel, dim3((unsigned)grid), dim3(e->threads_per_block), args, (size_t)e->smem_bytes,
                               s);
     } else {
-        void* args[] = {&in2, &out2, &batch, &tw, &scale, &err, &wait_ns};
+        int stall = 0;
+        void* args[] = {&in2, &out2, &batch, &tw, &scale, &err, &wait_ns, &stall};
         ce = cudaLaunchKernel(kernel, dim3((unsigned)grid), dim3(e->threads_per_block), args, (size_t)e->smem_bytes,
                               s);
     }

@@ -90,7 +90,8 @@ int occupancy_without_tmem(const void* kernel, int threads, int smem_bytes, int 
     return n < blk_sm ? n : blk_sm;
 }
 
-constexpr uint32_t kKnownFlags = FFT_FLAG_UNNORMALIZED | FFT_FLAG_SCALE_FORWARD | FFT_FLAG_VARIANT_MASK;
+constexpr uint32_t kKnownFlags =
+    FFT_FLAG_UNNORMALIZED | FFT_FLAG_SCALE_FORWARD | FFT_FLAG_VARIANT_MASK | FFT_FLAG_TEST_STALL;
 constexpr uint64_t kDefaultWaitNs = 4000000000ull;  // bounded device waits: 4 s
 
 }  // namespace
@@ -388,7 +389,8 @@ fft_status_t fft_execute(fft_plan_t p, const void* in, void* out, void* stream) 
         ce = cudaLaunchKernel(p->kernel, dim3((unsigned)p->grid), dim3(e->threads_per_block), args,
                               (size_t)e->smem_bytes, (cudaStream_t)stream);
     } else {
-        void* args[] = {&in2, &out2, &batch, &tw, &scale, &err, &wait_ns};
+        int stall = (p->flags & FFT_FLAG_TEST_STALL) ? 1 : 0;
+        void* args[] = {&in2, &out2, &batch, &tw, &scale, &err, &wait_ns, &stall};
         ce = cudaLaunchKernel(p->kernel, dim3((unsigned)p->grid), dim3(e->threads_per_block), args,
                               (size_t)e->smem_bytes, (cudaStream_t)stream);
     }
