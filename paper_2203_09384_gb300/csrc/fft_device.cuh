@@ -826,51 +826,60 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
 // tile of 32 signals through shared memory with coalesced 128-bit copies, so
 // HBM sees fully used sectors while each thread reads its own signal.
 // ---------------------------------------------------------------------------
-template <int LOG2N, int WARPS>
+template <int LOG2N, int WARPS, int U = 1>
 struct SmallCfg {
     static constexpr int N = 1 << LOG2N;
     static constexpr int H = N / 2;  // float4 slots per signal
     static constexpr int WARPS_PER_BLOCK = WARPS;
+    static constexpr int UNROLL = U;  // 32-signal groups a warp keeps in flight per iteration
     static constexpr int NT = 32 * WARPS;
-    static constexpr int kSmemBytes = WARPS * 32 * H * 16;
+    static constexpr int kSmemBytes = WARPS * 32 * U * H * 16;
 };
 
+// One warp tile = 32*U consecutive signals (contiguous in HBM): loaded with
+// coalesced 128-bit copies into the warp's shared-memory slab, then each lane
+// transforms U signals of its own, then the slab is stored back the same way.
 template <class SC, bool INV>
 __global__ void __launch_bounds__(SC::NT) fft_small_kernel(const float2* in, float2* out, int64_t batch,
                                                            float scale) {
-    constexpr int N = SC::N, H = SC::H, W = SC::WARPS_PER_BLOCK;
+    constexpr int N = SC::N, H = SC::H, W = SC::WARPS_PER_BLOCK, U = SC::UNROLL;
+    constexpr int TS = 32 * U;  // signals per warp tile
     extern __shared__ __align__(16) float4 smem4[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float4* sm = smem4 + warp * (32 * H);
-    const int64_t wtiles = (batch + 31) / 32;
+    float4* sm = smem4 + warp * (TS * H);
+    const int64_t wtiles = (batch + TS - 1) / TS;
     for (int64_t wt = (int64_t)blockIdx.x * W + warp; wt < wtiles; wt += (int64_t)gridDim.x * W) {
-        const int64_t first = wt * 32;
+        const int64_t first = wt * TS;
         const int64_t left = batch - first;
-        const int valid4 = (int)((left < 32 ? left : 32) * H);
+        const int valid4 = (int)((left < TS ? left : TS) * H);
         const float4* src = reinterpret_cast<const float4*>(in + first * N);
         float4* dst = reinterpret_cast<float4*>(out + first * N);
 #pragma unroll
-        for (int i = 0; i < H; ++i) {
+        for (int i = 0; i < U * H; ++i) {
             const int p = lane + 32 * i;
             if (p < valid4) sm[swz16(p)] = __ldcs(src + p);
         }
         __syncwarp();
-        float2 v[N];
 #pragma unroll
-        for (int i = 0; i < H; ++i) {
-            float4 f = sm[swz16(lane * H + i)];
-            v[2 * i] = make_float2(f.x, INV ? -f.y : f.y);
-            v[2 * i + 1] = make_float2(f.z, INV ? -f.w : f.w);
+        for (int u = 0; u < U; ++u) {
+            const int sig = u * 32 + lane;
+            float2 v[N];
+#pragma unroll
+            for (int i = 0; i < H; ++i) {
+                float4 f = sm[swz16(sig * H + i)];
+                v[2 * i] = make_float2(f.x, INV ? -f.y : f.y);
+                v[2 * i + 1] = make_float2(f.z, INV ? -f.w : f.w);
+            }
+            Dft<N>::run(v);
+#pragma unroll
+            for (int i = 0; i < N; ++i) v[i] = make_float2(v[i].x * scale, (INV ? -v[i].y : v[i].y) * scale);
+#pragma unroll
+            for (int i = 0; i < H; ++i)
+                sm[swz16(sig * H + i)] = make_float4(v[2 * i].x, v[2 * i].y, v[2 * i + 1].x, v[2 * i + 1].y);
         }
-        Dft<N>::run(v);
-#pragma unroll
-        for (int i = 0; i < N; ++i) v[i] = make_float2(v[i].x * scale, (INV ? -v[i].y : v[i].y) * scale);
-#pragma unroll
-        for (int i = 0; i < H; ++i)
-            sm[swz16(lane * H + i)] = make_float4(v[2 * i].x, v[2 * i].y, v[2 * i + 1].x, v[2 * i + 1].y);
         __syncwarp();
 #pragma unroll
-        for (int i = 0; i < H; ++i) {
+        for (int i = 0; i < U * H; ++i) {
             const int p = lane + 32 * i;
             if (p < valid4) __stcs(dst + p, sm[swz16(p)]);
         }

@@ -66,7 +66,7 @@ static KernelEntry small_entry(int variant) {
     e.variant = variant;
     e.kind = KernelKind::Small;
     e.elems_per_thread = SC::N;
-    e.signals_per_block = 32 * SC::WARPS_PER_BLOCK;
+    e.signals_per_block = 32 * SC::UNROLL * SC::WARPS_PER_BLOCK;
     e.threads_per_block = SC::NT;
     e.smem_bytes = SC::kSmemBytes;
     e.num_stages = 1;
@@ -158,7 +158,7 @@ int GBFFT_ENTRIES_FN(GBFFT_LOG2N)(gbfft::KernelEntry* out, int max) {
     GBFFT_ONLY_##L(put(generic_entry<Cfg<L, E, S, R0, R1, R2, R3, MINB, PIPE, TC>>(V));)
     GBFFT_GENERIC_SCHEDULES(GBFFT_GX)
 #undef GBFFT_GX
-#define GBFFT_SX(L, V, W) GBFFT_ONLY_##L(put(small_entry<SmallCfg<L, W>>(V));)
+#define GBFFT_SX(L, V, W, U) GBFFT_ONLY_##L(put(small_entry<SmallCfg<L, W, U>>(V));)
     GBFFT_SMALL_SCHEDULES(GBFFT_SX)
 #undef GBFFT_SX
     return count;

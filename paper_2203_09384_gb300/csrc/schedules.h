@@ -20,7 +20,8 @@
 // shared-memory exchanges of every row for bank conflicts under the XOR
 // swizzle of fft_device.cuh (64-bit accesses resolve per half-warp).
 //
-// One-thread-per-signal rows (N <= 32): SX(log2N, variant, warps per block).
+// One-thread-per-signal rows (N <= 32): SX(log2N, variant, warps per block,
+// 32-signal groups per warp tile).
 #pragma once
 
 #define GBFFT_GENERIC_SCHEDULES(GX)                   \
@@ -48,11 +49,20 @@
     GX(11, 5, 16, 1, 8, 16, 16, 0, 3, 2, 2)
 
 #define GBFFT_SMALL_SCHEDULES(SX) \
-    SX(1, 0, 8)                   \
-    SX(2, 0, 8)                   \
-    SX(3, 0, 8)                   \
-    SX(4, 0, 8)                   \
-    SX(5, 0, 4)
+    SX(1, 0, 8, 1)                \
+    SX(1, 1, 8, 2)                \
+    SX(2, 0, 8, 4)                \
+    SX(2, 1, 8, 1)                \
+    SX(2, 2, 8, 2)                \
+    SX(2, 3, 4, 4)                \
+    SX(3, 0, 8, 4)                \
+    SX(3, 1, 8, 1)                \
+    SX(3, 2, 4, 4)                \
+    SX(4, 0, 4, 2)                \
+    SX(4, 1, 8, 1)                \
+    SX(4, 2, 8, 2)                \
+    SX(5, 0, 2, 2)                \
+    SX(5, 2, 4, 1)
 
 #define GBFFT_MIN_LOG2N 1
 #define GBFFT_MAX_LOG2N 11
