@@ -69,7 +69,10 @@ enum {
      * waits run out after the plan's wait limit and fft_plan_get_error
      * reports FFT_ERR_TIMEOUT.  The output is not written.  Plans of kernels
      * without device-side waits ignore it. */
-    FFT_FLAG_TEST_STALL = 1u << 16
+    FFT_FLAG_TEST_STALL = 1u << 16,
+    /* Give the plan device staging buffers (three chunks of about 64 MiB)
+     * and three internal streams so that fft_execute_host can be used. */
+    FFT_FLAG_HOST_STAGING = 1u << 17
 };
 #define FFT_FLAG_VARIANT(k) ((uint32_t)((k) + 1) << 8)
 
@@ -139,6 +142,23 @@ GBFFT_API fft_status_t fft_plan_create_ex(int64_t n, int64_t batch, int directio
  * FFT_ERR_CUDA (launch failure, reported from cudaGetLastError).
  */
 GBFFT_API fft_status_t fft_execute(fft_plan_t plan, const void* in, void* out, void* stream);
+
+/*
+ * The planned transform on HOST buffers: batch*n complex64 read from
+ * `in_host`, results written to `out_host` (equal, or not overlapping).  The
+ * plan must have been made with FFT_FLAG_HOST_STAGING.  Work is split into
+ * chunks of whole signals; each chunk is copied to one of the plan's device
+ * buffers, transformed in place and copied back, the chunks round-robin over
+ * the plan's three streams so that host-to-device copies, kernels and
+ * device-to-host copies overlap.  Asynchronous with respect to the host: the
+ * pipeline starts after work already enqueued on `stream` and `stream` waits
+ * for its end (synchronise `stream` before reading out_host).  Host buffers
+ * should be page-locked (cudaHostAlloc / cudaHostRegister); pageable memory
+ * works but the copies then serialise.  One call at a time per plan.
+ * Errors: FFT_ERR_INVALID_VALUE (no staging, NULL, ragged plan, wrong device),
+ * FFT_ERR_OVERLAP, FFT_ERR_CUDA.
+ */
+GBFFT_API fft_status_t fft_execute_host(fft_plan_t plan, const void* in_host, void* out_host, void* stream);
 
 /*
  * Read and clear the plan's device error word (FFT_OK when no device-side

@@ -23,7 +23,8 @@ from ._abi import (FFT_C64, FFT_C64_TC_BF16, FFT_C64_TC_F16, FFT_FLAG_SCALE_FORW
                    fft_set_default_variant, fft_variant_count,
                    FFT_FORWARD, FFT_INVERSE, FFTError, STATUS, fft_execute, fft_plan_create,
                    fft_plan_create_ex, fft_plan_destroy, fft_plan_get_error, fft_plan_get_info,
-                   fft_plan_set_wait_limit, FFT_FLAG_TEST_STALL,
+                   fft_plan_set_wait_limit, FFT_FLAG_TEST_STALL, FFT_FLAG_HOST_STAGING,
+                   fft_execute_host,
                    fft_validate, lib)
 
 __all__ = ["Plan", "RaggedPlan", "fft", "ifft", "FFTFunction", "IFFTFunction", "fft_plan_create",
@@ -43,7 +44,7 @@ class Plan:
 
     def __init__(self, n: int, batch: int, inverse: bool = False, dtype: str = "c64",
                  normalized: bool = True, device=None, scale_forward: bool = False,
-                 variant: int | None = None, extra_flags: int = 0):
+                 variant: int | None = None, extra_flags: int = 0, host_staging: bool = False):
         self.n, self.batch, self.inverse = int(n), int(batch), bool(inverse)
         self.dtype = dtype
         self.normalized = normalized
@@ -55,6 +56,8 @@ class Plan:
         if variant is not None:
             flags |= FFT_FLAG_VARIANT(variant)
         flags |= int(extra_flags)
+        if host_staging:
+            flags |= FFT_FLAG_HOST_STAGING
         direction = FFT_INVERSE if inverse else FFT_FORWARD
         self.handle = None
         with torch.cuda.device(self.device):
@@ -77,6 +80,21 @@ class Plan:
         with torch.cuda.device(x.device):
             s = stream if stream is not None else torch.cuda.current_stream(x.device)
             fft_execute(self.handle, x.data_ptr(), out.data_ptr(), s.cuda_stream)
+        return out
+
+    def execute_host(self, x: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """Transform a host (CPU, ideally pinned) tensor through the plan's
+        chunked copy/transform/copy pipeline; synchronises the stream."""
+        if x.dtype != torch.complex64 or x.is_cuda or not x.is_contiguous():
+            raise TypeError("expected a contiguous complex64 CPU tensor")
+        if x.numel() != self.n * self.batch:
+            raise ValueError(f"tensor has {x.numel()} elements, plan wants {self.n * self.batch}")
+        if out is None:
+            out = torch.empty(x.shape, dtype=x.dtype, pin_memory=x.is_pinned())
+        with torch.cuda.device(self.device):
+            s = stream if stream is not None else torch.cuda.current_stream(self.device)
+            fft_execute_host(self.handle, x.data_ptr(), out.data_ptr(), s.cuda_stream)
+            s.synchronize()
         return out
 
     def error(self) -> int:

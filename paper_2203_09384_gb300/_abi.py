@@ -22,6 +22,7 @@ FFT_FLAG_UNNORMALIZED = 1 << 0
 FFT_FLAG_SCALE_FORWARD = 1 << 1
 FFT_FLAG_VARIANT_MASK = 0xF << 8
 FFT_FLAG_TEST_STALL = 1 << 16
+FFT_FLAG_HOST_STAGING = 1 << 17
 
 
 def FFT_FLAG_VARIANT(k: int) -> int:
@@ -114,6 +115,8 @@ def lib() -> ctypes.CDLL:
     L.fft_plan_create.argtypes = [_i64, _i64, _int, _int, ctypes.POINTER(_vp)]
     L.fft_plan_create_ex.restype = _int
     L.fft_plan_create_ex.argtypes = [_i64, _i64, _int, _int, _u32, ctypes.POINTER(_vp)]
+    L.fft_execute_host.restype = _int
+    L.fft_execute_host.argtypes = [_vp, _vp, _vp, _vp]
     L.fft_execute.restype = _int
     L.fft_execute.argtypes = [_vp, _vp, _vp, _vp]
     L.fft_plan_get_error.restype = _int
@@ -236,3 +239,7 @@ DTYPE_NAMES = {FFT_C64: "c64", FFT_C64_TC_F16: "tc_f16", FFT_C64_TC_BF16: "tc_bf
 
 def fft_variant_dtype(n: int, variant: int) -> int:
     return lib().fft_variant_dtype(n, variant)
+
+
+def fft_execute_host(plan: int, in_host: int, out_host: int, stream: int = 0) -> None:
+    check(lib().fft_execute_host(plan, in_host, out_host, stream), "fft_execute_host")

@@ -91,7 +91,8 @@ int occupancy_without_tmem(const void* kernel, int threads, int smem_bytes, int 
 }
 
 constexpr uint32_t kKnownFlags =
-    FFT_FLAG_UNNORMALIZED | FFT_FLAG_SCALE_FORWARD | FFT_FLAG_VARIANT_MASK | FFT_FLAG_TEST_STALL;
+    FFT_FLAG_UNNORMALIZED | FFT_FLAG_SCALE_FORWARD | FFT_FLAG_VARIANT_MASK | FFT_FLAG_TEST_STALL |
+    FFT_FLAG_HOST_STAGING;
 constexpr uint64_t kDefaultWaitNs = 4000000000ull;  // bounded device waits: 4 s
 
 }  // namespace
@@ -121,8 +122,97 @@ struct gbfft_plan {
     int64_t grid = 0;
     float scale = 1.0f;
     uint64_t wait_ns = kDefaultWaitNs;
+    int64_t resident = 0;                  // blocks that fit on the device at once
     gbfft::RaggedState* ragged = nullptr;  // set for mixed-length plans
+    // host-buffer pipeline (FFT_FLAG_HOST_STAGING): device chunk buffers,
+    // one stream each, and the events that tie them to the caller's stream
+    int stages = 0;
+    int64_t chunk_signals = 0;
+    float2* d_stage = nullptr;
+    cudaStream_t stage_stream[3] = {};
+    cudaEvent_t stage_done[3] = {};
+    cudaEvent_t stage_start = nullptr;
 };
+
+namespace {
+
+// One launch of the plan's kernel over `batch` signals (any batch up to the
+// plan's), grid sized for that batch.
+fft_status_t launch_plain(gbfft_plan* p, const float2* in2, float2* out2, int64_t batch, cudaStream_t stream) {
+    const KernelEntry* e = p->entry;
+    const int64_t tiles = (batch + e->signals_per_block - 1) / e->signals_per_block;
+    const int64_t grid = tiles < p->resident ? tiles : p->resident;
+    const float2* tw = (const float2*)p->d_twiddles;
+    float scale = p->scale;
+    int* err = p->d_error;
+    uint64_t wait_ns = p->wait_ns;
+    cudaError_t ce;
+    if (e->kind == KernelKind::Small) {
+        void* args[] = {&in2, &out2, &batch, &scale};
+        ce = cudaLaunchKernel(p->kernel, dim3((unsigned)grid), dim3(e->threads_per_block), args,
+                              (size_t)e->smem_bytes, stream);
+    } else {
+        int stall = (p->flags & FFT_FLAG_TEST_STALL) ? 1 : 0;
+        void* args[] = {&in2, &out2, &batch, &tw, &scale, &err, &wait_ns, &stall};
+        ce = cudaLaunchKernel(p->kernel, dim3((unsigned)grid), dim3(e->threads_per_block), args,
+                              (size_t)e->smem_bytes, stream);
+    }
+    if (ce != cudaSuccess) {
+        cudaGetLastError();
+        return FFT_ERR_CUDA;
+    }
+    return FFT_OK;
+}
+
+void release_staging(gbfft_plan* p) {
+    for (int i = 0; i < 3; ++i) {
+        if (p->stage_stream[i]) cudaStreamDestroy(p->stage_stream[i]);
+        if (p->stage_done[i]) cudaEventDestroy(p->stage_done[i]);
+        p->stage_stream[i] = nullptr;
+        p->stage_done[i] = nullptr;
+    }
+    if (p->stage_start) cudaEventDestroy(p->stage_start);
+    if (p->d_stage) cudaFree(p->d_stage);
+    p->stage_start = nullptr;
+    p->d_stage = nullptr;
+    p->stages = 0;
+}
+
+// Chunk buffers for fft_execute_host: three of about 64 MiB each (whole tiles
+// of signals), transformed in place.
+fft_status_t create_staging(gbfft_plan* p) {
+    const int64_t sig_bytes = p->n * 8;
+    const int64_t S = p->entry->signals_per_block;
+    int64_t chunk = (int64_t(64) << 20) / sig_bytes;
+    chunk = chunk / S * S;
+    if (chunk < S) chunk = S;
+    if (chunk > p->batch) chunk = p->batch;
+    if (chunk < 1) chunk = 1;
+    p->chunk_signals = chunk;
+    p->stages = 3;
+    if (cudaMalloc(&p->d_stage, (size_t)(3 * chunk * sig_bytes)) != cudaSuccess) {
+        cudaGetLastError();
+        p->d_stage = nullptr;
+        p->stages = 0;
+        return FFT_ERR_ALLOC;
+    }
+    for (int i = 0; i < 3; ++i) {
+        if (cudaStreamCreateWithFlags(&p->stage_stream[i], cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&p->stage_done[i], cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            release_staging(p);
+            return FFT_ERR_CUDA;
+        }
+    }
+    if (cudaEventCreateWithFlags(&p->stage_start, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        release_staging(p);
+        return FFT_ERR_CUDA;
+    }
+    return FFT_OK;
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -312,7 +402,16 @@ fft_status_t fft_plan_create_ex(int64_t n, int64_t batch, int direction, int dty
         return FFT_ERR_UNSUPPORTED;
     }
     const int64_t resident = (int64_t)sms * per_sm;
+    p->resident = resident;
     p->grid = tiles < resident ? tiles : resident;
+    if ((flags & FFT_FLAG_HOST_STAGING) && batch > 0) {
+        fft_status_t sst = create_staging(p);
+        if (sst != FFT_OK) {
+            cudaFree(dmem);
+            delete p;
+            return sst;
+        }
+    }
     *plan = p;
     return FFT_OK;
 }
@@ -375,30 +474,55 @@ fft_status_t fft_execute(fft_plan_t p, const void* in, void* out, void* stream) 
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev != p->device) return FFT_ERR_INVALID_VALUE;
 
-    const KernelEntry* e = p->entry;
-    const float2* in2 = (const float2*)in;
-    float2* out2 = (float2*)out;
-    int64_t batch = p->batch;
-    const float2* tw = (const float2*)p->d_twiddles;
-    float scale = p->scale;
-    int* err = p->d_error;
-    uint64_t wait_ns = p->wait_ns;
-    cudaError_t ce;
-    if (e->kind == KernelKind::Small) {
-        void* args[] = {&in2, &out2, &batch, &scale};
-        ce = cudaLaunchKernel(p->kernel, dim3((unsigned)p->grid), dim3(e->threads_per_block), args,
-                              (size_t)e->smem_bytes, (cudaStream_t)stream);
-    } else {
-        int stall = (p->flags & FFT_FLAG_TEST_STALL) ? 1 : 0;
-        void* args[] = {&in2, &out2, &batch, &tw, &scale, &err, &wait_ns, &stall};
-        ce = cudaLaunchKernel(p->kernel, dim3((unsigned)p->grid), dim3(e->threads_per_block), args,
-                              (size_t)e->smem_bytes, (cudaStream_t)stream);
+    return launch_plain(p, (const float2*)in, (float2*)out, p->batch, (cudaStream_t)stream);
+}
+
+fft_status_t fft_execute_host(fft_plan_t p, const void* in_host, void* out_host, void* stream) {
+    if (!p || p->ragged) return FFT_ERR_INVALID_VALUE;
+    if (p->batch == 0) return FFT_OK;
+    if (!p->stages) return FFT_ERR_INVALID_VALUE;  // plan made without FFT_FLAG_HOST_STAGING
+    if (!in_host || !out_host) return FFT_ERR_INVALID_VALUE;
+    const uintptr_t bytes = (uintptr_t)(p->n * p->batch * 8);
+    const uintptr_t a = (uintptr_t)in_host, b = (uintptr_t)out_host;
+    if (a != b && a < b + bytes && b < a + bytes) return FFT_ERR_OVERLAP;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != p->device) return FFT_ERR_INVALID_VALUE;
+    cudaStream_t user = (cudaStream_t)stream;
+    // the pipeline starts after the caller's earlier work ...
+    if (cudaEventRecord(p->stage_start, user) != cudaSuccess) goto cuda_fail;
+    for (int i = 0; i < p->stages; ++i)
+        if (cudaStreamWaitEvent(p->stage_stream[i], p->stage_start, 0) != cudaSuccess) goto cuda_fail;
+    {
+        const int64_t sig_bytes = p->n * 8;
+        const char* src = static_cast<const char*>(in_host);
+        char* dst = static_cast<char*>(out_host);
+        int64_t k = 0;
+        for (int64_t first = 0; first < p->batch; first += p->chunk_signals, ++k) {
+            const int i = (int)(k % p->stages);
+            const int64_t nsig = p->batch - first < p->chunk_signals ? p->batch - first : p->chunk_signals;
+            const size_t nbytes = (size_t)(nsig * sig_bytes);
+            float2* buf = p->d_stage + (size_t)i * p->chunk_signals * p->n;
+            cudaStream_t s = p->stage_stream[i];
+            // in one stream a chunk's copy in, transform and copy out stay in
+            // order; the three streams overlap both copy directions and kernels
+            if (cudaMemcpyAsync(buf, src + first * sig_bytes, nbytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
+                goto cuda_fail;
+            fft_status_t st = launch_plain(p, buf, buf, nsig, s);
+            if (st != FFT_OK) return st;
+            if (cudaMemcpyAsync(dst + first * sig_bytes, buf, nbytes, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+                goto cuda_fail;
+        }
     }
-    if (ce != cudaSuccess) {
-        cudaGetLastError();
-        return FFT_ERR_CUDA;
+    // ... and the caller's stream resumes once every chunk is back on the host
+    for (int i = 0; i < p->stages; ++i) {
+        if (cudaEventRecord(p->stage_done[i], p->stage_stream[i]) != cudaSuccess ||
+            cudaStreamWaitEvent(user, p->stage_done[i], 0) != cudaSuccess)
+            goto cuda_fail;
     }
     return FFT_OK;
+cuda_fail:
+    cudaGetLastError();
+    return FFT_ERR_CUDA;
 }
 
 fft_status_t fft_plan_get_error(fft_plan_t p) {
@@ -417,6 +541,7 @@ fft_status_t fft_plan_destroy(fft_plan_t p) {
     if (!p) return FFT_OK;
     fft_status_t st = FFT_OK;
     if (p->d_twiddles && cudaFree(p->d_twiddles) != cudaSuccess) st = FFT_ERR_CUDA;
+    release_staging(p);
     gbfft::ragged_destroy(p->ragged);
     delete p;
     return st;

@@ -231,3 +231,26 @@ def test_full_size_sampled(n):
     plan.close()
     del x, out
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("n,batch", [(2, 70001), (64, 3 * 2 ** 20 // 64 + 5), (2048, 9001), (256, 1)])
+def test_execute_host_pipeline(n, batch):
+    """fft_execute_host: pinned host buffers, chunked copy / transform / copy
+    over the plan's streams; chunk tails and single-chunk batches."""
+    x = synth.uniform(batch, n, seed=41).pin_memory()
+    plan = gb.Plan(n, batch, host_staging=True)
+    y = plan.execute_host(x)
+    assert plan.error() == 0
+    rng = np.random.default_rng(n)
+    idx = np.unique(np.concatenate([[0, batch - 1], rng.integers(0, batch, 300)]))
+    assert max_rel_l2(y.numpy()[idx], oracle_of(x[idx])) <= FP32_TOL
+    # in place on the host
+    z = x.clone().pin_memory()
+    plan.execute_host(z, z)
+    assert torch.equal(z, y)
+    plan.close()
+    # a plan made without staging refuses host execution
+    p2 = gb.Plan(n, batch)
+    with pytest.raises(gb.FFTError):
+        p2.execute_host(x)
+    p2.close()
