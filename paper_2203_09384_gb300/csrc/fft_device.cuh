@@ -264,7 +264,8 @@ constexpr int kErrTimeout = 8;
 // ---------------------------------------------------------------------------
 // Compile-time schedule
 // ---------------------------------------------------------------------------
-template <int LOG2N_, int E_, int S_, int R0, int R1, int R2, int R3, int MINB_ = 1, int PIPE_ = 0, int TC_ = 0>
+template <int LOG2N_, int E_, int S_, int R0, int R1, int R2, int R3, int MINB_ = 1, int PIPE_ = 0, int TC_ = 0,
+          int XB_ = 0>
 struct Cfg {
     static constexpr int LOG2N = LOG2N_;
     static constexpr int N = 1 << LOG2N_;
@@ -275,8 +276,13 @@ struct Cfg {
     static constexpr int MINB = MINB_;    // min resident blocks per SM (launch bounds)
     static constexpr int PIPE = PIPE_;    // 0: direct loads; D: bulk-copy ring of D tiles
     static constexpr int M = (R0 > 0) + (R1 > 0) + (R2 > 0) + (R3 > 0);
-    static constexpr bool kWarpLocal = T <= 32;  // a signal never spans warps
-    static constexpr int kBuffers = kWarpLocal ? 1 : 2;
+    // a signal never spans warps, so exchanges need only warp syncs (the
+    // bulk-copy ring refills after a block-wide barrier, so it uses those)
+    static constexpr bool kWarpLocal = T <= 32 && PIPE_ == 0;
+    // exchange buffers: one suffices when a signal stays in one warp; across
+    // warps two let one barrier per exchange do (XB = 1 forces one buffer and
+    // a second barrier, halving the shared memory of the exchange)
+    static constexpr int kBuffers = XB_ ? XB_ : (kWarpLocal ? 1 : 2);
     static constexpr int kSmemElems = kBuffers * S * N;           // exchange buffers
     static constexpr int kRingElems = PIPE * S * N;               // prefetch ring
     // 0: FP32 butterflies; 1 / 2: radix-16 stages on FP16 / BF16 tensor cores
@@ -308,8 +314,7 @@ struct Cfg {
     static_assert(E % R0 == 0 && E % (R1 ? R1 : 1) == 0 && E % (R2 ? R2 : 1) == 0 && E % (R3 ? R3 : 1) == 0,
                   "every radix must divide E");
     static_assert(32 % T == 0 || T % 32 == 0, "T must tile warps");
-    static_assert(PIPE == 0 || (PIPE >= 2 && !kWarpLocal),
-                  "the bulk-copy ring needs block-wide exchanges (T > 32)");
+    static_assert(PIPE == 0 || PIPE >= 2, "the bulk-copy ring needs at least two slots");
     static_assert(TC == 0 || (E == 16 && NT % 128 == 0 && (kTcCols == 32 || kTcCols == 64 || kTcCols == 128)),
                   "tensor-core radix-16 stages need one 16-point butterfly per thread and 128-row tiles");
 };
@@ -334,7 +339,6 @@ struct TcCtx {
     unsigned char* a = nullptr;
     unsigned char* b = nullptr;
     uint64_t* bar = nullptr;
-    float* red = nullptr;  // per-warp slots for the per-signal maximum
     int* err = nullptr;
     uint64_t wait_ns = 0;
     bool dead = false;   // a bounded wait gave up: stop waiting, finish
@@ -398,7 +402,6 @@ __device__ __forceinline__ void tc_setup(TcCtx& tc, unsigned char* base, int* er
     tc.b = base + C::kTcTiles * 8192;
     tc.bar = reinterpret_cast<uint64_t*>(tc.b + 2048);
     uint32_t* slot = reinterpret_cast<uint32_t*>(tc.b + 2048 + 8);
-    tc.red = reinterpret_cast<float*>(tc.b + 2048 + 64);
     tc.err = err;
     tc.wait_ns = wait_ns;
     if ((threadIdx.x >> 5) == 0) {
@@ -441,10 +444,23 @@ __device__ __forceinline__ void tc_teardown(TcCtx& tc) {
 }
 
 // Every thread of the block calls this with its own butterfly's 16 inputs.
+// The 16-point DFT is linear, so each row is scaled by its own power of two
+// 2^-e (exact) before the FP16/BF16 conversion, which keeps every operand in
+// [-1, 1) whatever the signal's magnitude, and the FP32 accumulators are
+// multiplied by 2^e after the read-back.
 template <class C>
 __device__ __forceinline__ void tc_dft16(float2* v, TcCtx& tc) {
     const int tid = threadIdx.x;
     const int row = tid & 127;
+    float mx = 0.0f;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) mx = fmaxf(mx, fmaxf(fabsf(v[i].x), fabsf(v[i].y)));
+    int e = 0;
+    frexpf(mx, &e);
+    e = mx > 0.0f ? (e < -120 ? -120 : e) : 0;
+    const float down = ldexpf(1.0f, -e), up = ldexpf(1.0f, e);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = make_float2(v[i].x * down, v[i].y * down);
     unsigned char* arow = tc.a + (tid >> 7) * 8192 + (row >> 3) * 512 + (row & 7) * 16;
 #pragma unroll
     for (int c = 0; c < 4; ++c) {  // K chunk c: Re x_0..7, Re x_8..15, Im x_0..7, Im x_8..15
@@ -506,35 +522,8 @@ __device__ __forceinline__ void tc_dft16(float2* v, TcCtx& tc) {
         : "r"(taddr));
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-    for (int q = 0; q < 16; ++q) v[q] = make_float2(__uint_as_float(r[q]), __uint_as_float(r[16 + q]));
+    for (int q = 0; q < 16; ++q) v[q] = make_float2(__uint_as_float(r[q]) * up, __uint_as_float(r[16 + q]) * up);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-
-// Per-signal power-of-two prescale for the tensor-core path: returns e with
-// max(|Re|, |Im|) * 2^-e < 1 over the signal (0 for an all-zero signal).
-template <class C>
-__device__ __forceinline__ int tc_signal_exponent(const float2 (&v)[C::E], TcCtx& tc) {
-    float m = 0.0f;
-#pragma unroll
-    for (int i = 0; i < C::E; ++i) m = fmaxf(m, fmaxf(fabsf(v[i].x), fabsf(v[i].y)));
-    if constexpr (C::T <= 32) {
-#pragma unroll
-        for (int o = 1; o < C::T; o <<= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-    } else {
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-        const int warp = threadIdx.x >> 5;
-        if ((threadIdx.x & 31) == 0) tc.red[warp] = m;
-        __syncthreads();
-        constexpr int W = C::T / 32;
-        const int w0 = (warp / W) * W;
-        m = 0.0f;
-#pragma unroll
-        for (int w = 0; w < W; ++w) m = fmaxf(m, tc.red[w0 + w]);
-    }
-    int e = 0;
-    frexpf(m, &e);
-    return m > 0.0f ? e : 0;
 }
 
 // Butterfly handled by thread t in slot c of stage s.  The first and the last
@@ -668,7 +657,13 @@ __device__ __forceinline__ void rest_stages(float2 (&v)[C::E], float2* smem, int
                                             const float2* __restrict__ tw, TcCtx& tc) {
     if constexpr (s < C::M) {
         float2* b = smem + buf * (C::S * C::N);
-        if constexpr (C::kWarpLocal) __syncwarp();  // previous readers of b are done
+        if constexpr (C::kBuffers == 1) {  // previous readers of b are done
+            if constexpr (C::kWarpLocal) {
+                __syncwarp();
+            } else {
+                __syncthreads();
+            }
+        }
         scatter<C, s - 1>(v, b, sb, t);
         exchange_barrier<C>();
         gather<C, s>(v, b, sb, t);
@@ -699,17 +694,9 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
         const int64_t base = sig * C::N;
         float2 v[C::E];
         load_first<C, INV>(v, in + base, t, active);
-        float sc = scale;
-        if constexpr (C::TC != 0) {
-            const int e = tc_signal_exponent<C>(v, tc);
-            const float f = ldexpf(1.0f, -e);
-#pragma unroll
-            for (int i = 0; i < C::E; ++i) v[i] = make_float2(v[i].x * f, v[i].y * f);
-            sc = ldexpf(scale, e);
-        }
         twist_and_dft<C, 0>(v, t, tw, tc);
         rest_stages<C, 1>(v, smem, buf, sb, t, tw, tc);
-        store_last<C, INV>(v, out + base, t, active && !tc.dead, sc);
+        store_last<C, INV>(v, out + base, t, active && !tc.dead, scale);
     }
     if constexpr (C::TC != 0) tc_teardown<C>(tc);
 }
@@ -792,16 +779,9 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
         const int64_t sig = tile * C::S + sl;
         float2 v[C::E];
         gather_tile<C, INV>(v, ring + slot * TILE, sb, t);
-        float sc = scale;
-        if constexpr (C::TC != 0) {
-            const int e = tc_signal_exponent<C>(v, tc);
-            const float f = ldexpf(1.0f, -e);
-#pragma unroll
-            for (int i = 0; i < C::E; ++i) v[i] = make_float2(v[i].x * f, v[i].y * f);
-            sc = ldexpf(scale, e);
-        }
         twist_and_dft<C, 0>(v, t, tw, tc);
         float2* b = smem + buf * TILE;
+        if constexpr (C::kBuffers == 1) __syncthreads();  // previous readers of b are done
         scatter<C, 0>(v, b, sb, t);
         __syncthreads();  // every thread is done with ring[slot]
         if (tid == 0 && !dead && !stall) {
@@ -812,11 +792,11 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
             }
         }
         gather<C, 1>(v, b, sb, t);
-        buf ^= 1;
+        if constexpr (C::kBuffers == 2) buf ^= 1;
         twist_and_dft<C, 1>(v, t, tw, tc);
         rest_stages<C, 2>(v, smem, buf, sb, t, tw, tc);
         const bool active = sig < batch && !dead && !tc.dead;
-        store_last<C, INV>(v, out + sig * C::N, t, active, sc);
+        store_last<C, INV>(v, out + sig * C::N, t, active, scale);
     }
     if constexpr (C::TC != 0) tc_teardown<C>(tc);
 }

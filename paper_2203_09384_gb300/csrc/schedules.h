@@ -13,7 +13,9 @@
 //             (TMA) prefetch, D-1 tiles ahead of the one being transformed,
 //      TC = 0: FP32 butterflies; 1 / 2: every radix-16 stage runs as a dense
 //           16 x 16 complex product on FP16 / BF16 tensor cores (tcgen05),
-//           FP32 accumulation, per-signal power-of-two prescale)
+//           FP32 accumulation, per-signal power-of-two prescale,
+//      XB = exchange buffers: 0 = automatic, 1 = one buffer and two barriers
+//           per exchange (less shared memory, more resident blocks))
 // Threads per block = S * N / E.  Stage 0 with R0 = E/2 (and the last stage,
 // where its radix is E/2 or less) lets a thread own neighbouring butterflies,
 // so its HBM accesses are 128-bit.  An index model on the host checked the
@@ -25,28 +27,36 @@
 #pragma once
 
 #define GBFFT_GENERIC_SCHEDULES(GX)                   \
-    GX(5, 1, 16, 128, 8, 4, 0, 0, 1, 0, 0) \
-    GX(6, 0, 16, 64, 8, 8, 0, 0, 1, 0, 0) \
-    GX(7, 0, 16, 32, 8, 16, 0, 0, 1, 0, 0) \
-    GX(8, 0, 16, 16, 16, 16, 0, 0, 1, 0, 0) \
-    GX(9, 0, 16, 8, 8, 8, 8, 0, 2, 0, 0) \
-    GX(9, 1, 16, 8, 8, 8, 8, 0, 1, 0, 0) \
-    GX(10, 0, 16, 2, 8, 16, 8, 0, 2, 2, 0) \
-    GX(10, 1, 16, 2, 8, 16, 8, 0, 1, 0, 0) \
-    GX(10, 2, 16, 2, 8, 16, 8, 0, 4, 0, 0) \
-    GX(10, 3, 16, 2, 8, 16, 8, 0, 2, 3, 0) \
-    GX(11, 0, 16, 1, 8, 16, 16, 0, 3, 2, 0) \
-    GX(11, 1, 16, 1, 8, 16, 16, 0, 1, 0, 0) \
-    GX(11, 2, 16, 1, 8, 16, 16, 0, 2, 3, 0) \
-    GX(11, 3, 16, 2, 8, 16, 16, 0, 1, 2, 0) \
-    GX(7, 1, 16, 32, 8, 16, 0, 0, 2, 0, 1) \
-    GX(7, 2, 16, 32, 8, 16, 0, 0, 2, 0, 2) \
-    GX(8, 1, 16, 16, 16, 16, 0, 0, 1, 0, 1) \
-    GX(8, 2, 16, 16, 16, 16, 0, 0, 1, 0, 2) \
-    GX(10, 4, 16, 2, 8, 16, 8, 0, 2, 2, 1) \
-    GX(10, 5, 16, 2, 8, 16, 8, 0, 2, 2, 2) \
-    GX(11, 4, 16, 1, 8, 16, 16, 0, 3, 2, 1) \
-    GX(11, 5, 16, 1, 8, 16, 16, 0, 3, 2, 2)
+    GX(5, 1, 16, 128, 8, 4, 0, 0, 1, 0, 0, 0) \
+    GX(6, 0, 16, 64, 8, 8, 0, 0, 1, 0, 0, 0) \
+    GX(7, 0, 16, 32, 8, 16, 0, 0, 1, 0, 0, 0) \
+    GX(7, 1, 16, 16, 8, 16, 0, 0, 3, 2, 1, 0) \
+    GX(7, 2, 16, 16, 8, 16, 0, 0, 3, 2, 2, 0) \
+    GX(7, 3, 16, 32, 8, 16, 0, 0, 2, 0, 1, 0) \
+    GX(7, 4, 16, 32, 8, 16, 0, 0, 2, 0, 2, 0) \
+    GX(8, 0, 16, 16, 16, 16, 0, 0, 1, 0, 0, 0) \
+    GX(8, 1, 16, 8, 16, 16, 0, 0, 3, 2, 1, 0) \
+    GX(8, 2, 16, 8, 16, 16, 0, 0, 3, 2, 2, 0) \
+    GX(8, 3, 16, 16, 16, 16, 0, 0, 1, 0, 1, 0) \
+    GX(8, 4, 16, 16, 16, 16, 0, 0, 1, 0, 2, 0) \
+    GX(9, 0, 16, 8, 8, 8, 8, 0, 2, 0, 0, 0) \
+    GX(9, 1, 16, 8, 8, 8, 8, 0, 1, 0, 0, 0) \
+    GX(10, 0, 16, 2, 8, 16, 8, 0, 2, 2, 0, 0) \
+    GX(10, 1, 16, 2, 8, 16, 8, 0, 1, 0, 0, 0) \
+    GX(10, 2, 16, 2, 8, 16, 8, 0, 4, 0, 0, 0) \
+    GX(10, 3, 16, 2, 8, 16, 8, 0, 2, 3, 0, 0) \
+    GX(10, 4, 16, 2, 8, 16, 8, 0, 4, 2, 1, 1) \
+    GX(10, 5, 16, 2, 8, 16, 8, 0, 4, 2, 2, 1) \
+    GX(10, 6, 16, 2, 8, 16, 8, 0, 2, 2, 1, 0) \
+    GX(10, 7, 16, 2, 8, 16, 8, 0, 2, 2, 2, 0) \
+    GX(11, 0, 16, 1, 8, 16, 16, 0, 3, 2, 0, 0) \
+    GX(11, 1, 16, 1, 8, 16, 16, 0, 1, 0, 0, 0) \
+    GX(11, 2, 16, 1, 8, 16, 16, 0, 2, 3, 0, 0) \
+    GX(11, 3, 16, 2, 8, 16, 16, 0, 1, 2, 0, 0) \
+    GX(11, 4, 16, 1, 8, 16, 16, 0, 4, 2, 1, 1) \
+    GX(11, 5, 16, 1, 8, 16, 16, 0, 4, 2, 2, 1) \
+    GX(11, 6, 16, 1, 8, 16, 16, 0, 3, 2, 1, 0) \
+    GX(11, 7, 16, 1, 8, 16, 16, 0, 3, 2, 2, 0)
 
 #define GBFFT_SMALL_SCHEDULES(SX) \
     SX(1, 0, 8, 1)                \

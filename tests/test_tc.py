@@ -86,3 +86,27 @@ def test_tc_accuracy_is_reported_not_hidden():
     e_bf = max_rel_l2(to_np(run(x.cuda(), 256, "tc_bf16")[0]), want)
     e32 = max_rel_l2(to_np(run(x.cuda(), 256, "c64")[0]), want)
     assert e32 < 1e-6 < e16 < e_bf <= TC_TOL, (e32, e16, e_bf)
+
+
+def _tc_variants():
+    out = []
+    for n in [2 ** k for k in range(1, 12)]:
+        for v in range(gb.fft_variant_count(n)):
+            dt = gb.fft_variant_dtype(n, v)
+            if dt != gb.FFT_C64:
+                out.append((n, v, gb.DTYPE_NAMES[dt]))
+    return out
+
+
+@pytest.mark.parametrize("n,variant,dtype", _tc_variants())
+def test_every_tensor_core_schedule(n, variant, dtype):
+    batch = 2 * 152 + 5
+    x, _ = synth.scaled_normal(batch, n, seed=6)
+    for inverse in (False, True):
+        plan = gb.Plan(n, batch, inverse=inverse, dtype=dtype, variant=variant)
+        out = plan.execute(x.cuda())
+        torch.cuda.synchronize()
+        assert plan.error() == 0 and plan.info().variant == variant
+        plan.close()
+        err = rel_l2_per_signal(to_np(out), oracle.reference(x.numpy(), inverse, threads=8))
+        assert err.max() <= TC_TOL, (n, variant, dtype, inverse, err.max())
