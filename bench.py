@@ -369,7 +369,7 @@ def run_ours(args):
         LOG2NS = [int(math.log2(int(v))) for v in args.only_n.split(",")]
     x = synth.uniform(1, ELEMS, seed=1 + rank, device=dev).reshape(-1)
     out = torch.empty_like(x)
-    plans = {k: gb.Plan(2 ** k, ELEMS // 2 ** k, device=dev) for k in LOG2NS}
+    plans = {k: gb.Plan(2 ** k, ELEMS // 2 ** k, device=dev, dtype=args.dtype) for k in LOG2NS}
 
     def step(events=None):
         for i, k in enumerate(LOG2NS):
@@ -466,7 +466,8 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"c64": "f32", "tc_f16": "f16-tensor-core+f32", "tc_bf16": "bf16-tensor-core+f32"}[args.dtype],
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "lengths": [2 ** k for k in LOG2NS],
                    "elements_per_length": ELEMS, "bytes_per_step_per_gpu": step_bytes,
@@ -502,6 +503,8 @@ def main(argv=None):
                     help="skip the adjoint / ragged / tensor-core workloads")
     ap.add_argument("--only-n", default="", help="comma list of lengths (profiling runs)")
     ap.add_argument("--elems", type=int, default=0, help="elements per length (profiling runs)")
+    ap.add_argument("--dtype", default="c64", choices=["c64", "tc_f16", "tc_bf16"],
+                    help="arithmetic of the sweep (profiling runs of the tensor-core path)")
     args = ap.parse_args(argv)
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
