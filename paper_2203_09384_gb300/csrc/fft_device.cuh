@@ -185,12 +185,57 @@ struct Dft<32> {
 // ---------------------------------------------------------------------------
 // memory helpers: streaming (evict-first) 64/128-bit global accesses
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float4 ld_stream4(const float2* p) { return __ldcs(reinterpret_cast<const float4*>(p)); }
-__device__ __forceinline__ float2 ld_stream2(const float2* p) { return __ldcs(p); }
-__device__ __forceinline__ void st_stream4(float2* p, float2 a, float2 b) {
-    __stcs(reinterpret_cast<float4*>(p), make_float4(a.x, a.y, b.x, b.y));
+// Cache hint per schedule (CH): bit 0 set = plain loads instead of
+// evict-first (.cs) loads, bit 1 set = plain stores instead of .cs stores.
+// Which is faster depends on the length (measured, see the schedule table).
+template <int CH>
+__device__ __forceinline__ float4 ld_stream4(const float2* p) {
+    if constexpr (CH & 1) {
+        return *reinterpret_cast<const float4*>(p);
+    } else {
+        return __ldcs(reinterpret_cast<const float4*>(p));
+    }
 }
-__device__ __forceinline__ void st_stream2(float2* p, float2 a) { __stcs(p, a); }
+template <int CH>
+__device__ __forceinline__ float2 ld_stream2(const float2* p) {
+    if constexpr (CH & 1) {
+        return *p;
+    } else {
+        return __ldcs(p);
+    }
+}
+template <int CH>
+__device__ __forceinline__ void st_stream4(float2* p, float2 a, float2 b) {
+    if constexpr (CH & 2) {
+        *reinterpret_cast<float4*>(p) = make_float4(a.x, a.y, b.x, b.y);
+    } else {
+        __stcs(reinterpret_cast<float4*>(p), make_float4(a.x, a.y, b.x, b.y));
+    }
+}
+template <int CH>
+__device__ __forceinline__ void st_stream2(float2* p, float2 a) {
+    if constexpr (CH & 2) {
+        *p = a;
+    } else {
+        __stcs(p, a);
+    }
+}
+template <int CH>
+__device__ __forceinline__ float4 ld_stream4v(const float4* p) {
+    if constexpr (CH & 1) {
+        return *p;
+    } else {
+        return __ldcs(p);
+    }
+}
+template <int CH>
+__device__ __forceinline__ void st_stream4v(float4* p, float4 a) {
+    if constexpr (CH & 2) {
+        *p = a;
+    } else {
+        __stcs(p, a);
+    }
+}
 
 // Shared-memory swizzle at 8-byte granularity: rows of 16 elements (128 B)
 // are XOR-permuted by their row index.  Keeps every Stockham exchange of the
@@ -265,8 +310,9 @@ constexpr int kErrTimeout = 8;
 // Compile-time schedule
 // ---------------------------------------------------------------------------
 template <int LOG2N_, int E_, int S_, int R0, int R1, int R2, int R3, int MINB_ = 1, int PIPE_ = 0, int TC_ = 0,
-          int XB_ = 0>
+          int XB_ = 0, int CH_ = 0>
 struct Cfg {
+    static constexpr int CH = CH_;  // cache hints of the HBM loads / stores
     static constexpr int LOG2N = LOG2N_;
     static constexpr int N = 1 << LOG2N_;
     static constexpr int E = E_;          // complex elements per thread
@@ -606,14 +652,14 @@ __device__ __forceinline__ void load_first(float2 (&v)[C::E], const float2* src,
         for (int r = 0; r < R; ++r) {
 #pragma unroll
             for (int c = 0; c < K; c += 2) {
-                float4 f = ld_stream4(src + K * t + c + r * stride);
+                float4 f = ld_stream4<C::CH>(src + K * t + c + r * stride);
                 v[c * R + r] = make_float2(f.x, f.y);
                 v[(c + 1) * R + r] = make_float2(f.z, f.w);
             }
         }
     } else {
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[r] = ld_stream2(src + t + r * stride);
+        for (int r = 0; r < R; ++r) v[r] = ld_stream2<C::CH>(src + t + r * stride);
     }
     if constexpr (INV) {
 #pragma unroll
@@ -634,11 +680,11 @@ __device__ __forceinline__ void store_last(float2 (&v)[C::E], float2* dst, int t
 #pragma unroll
         for (int q = 0; q < R; ++q) {
 #pragma unroll
-            for (int c = 0; c < K; c += 2) st_stream4(dst + K * t + c + q * stride, v[c * R + q], v[(c + 1) * R + q]);
+            for (int c = 0; c < K; c += 2) st_stream4<C::CH>(dst + K * t + c + q * stride, v[c * R + q], v[(c + 1) * R + q]);
         }
     } else {
 #pragma unroll
-        for (int q = 0; q < R; ++q) st_stream2(dst + t + q * stride, v[q]);
+        for (int q = 0; q < R; ++q) st_stream2<C::CH>(dst + t + q * stride, v[q]);
     }
 }
 
@@ -806,8 +852,9 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
 // tile of 32 signals through shared memory with coalesced 128-bit copies, so
 // HBM sees fully used sectors while each thread reads its own signal.
 // ---------------------------------------------------------------------------
-template <int LOG2N, int WARPS, int U = 1>
+template <int LOG2N, int WARPS, int U = 1, int CH_ = 0>
 struct SmallCfg {
+    static constexpr int CH = CH_;  // cache hints of the HBM loads / stores
     static constexpr int N = 1 << LOG2N;
     static constexpr int H = N / 2;  // float4 slots per signal
     static constexpr int WARPS_PER_BLOCK = WARPS;
@@ -837,7 +884,7 @@ __global__ void __launch_bounds__(SC::NT) fft_small_kernel(const float2* in, flo
 #pragma unroll
         for (int i = 0; i < U * H; ++i) {
             const int p = lane + 32 * i;
-            if (p < valid4) sm[swz16(p)] = __ldcs(src + p);
+            if (p < valid4) sm[swz16(p)] = ld_stream4v<SC::CH>(src + p);
         }
         __syncwarp();
 #pragma unroll
@@ -861,7 +908,7 @@ __global__ void __launch_bounds__(SC::NT) fft_small_kernel(const float2* in, flo
 #pragma unroll
         for (int i = 0; i < U * H; ++i) {
             const int p = lane + 32 * i;
-            if (p < valid4) __stcs(dst + p, sm[swz16(p)]);
+            if (p < valid4) st_stream4v<SC::CH>(dst + p, sm[swz16(p)]);
         }
         __syncwarp();
     }

@@ -154,11 +154,11 @@ int GBFFT_ENTRIES_FN(GBFFT_LOG2N)(gbfft::KernelEntry* out, int max) {
             if (e.variant + 1 > count) count = e.variant + 1;
         }
     };
-#define GBFFT_GX(L, V, E, S, R0, R1, R2, R3, MINB, PIPE, TC, XB) \
-    GBFFT_ONLY_##L(put(generic_entry<Cfg<L, E, S, R0, R1, R2, R3, MINB, PIPE, TC, XB>>(V));)
+#define GBFFT_GX(L, V, E, S, R0, R1, R2, R3, MINB, PIPE, TC, XB, CH) \
+    GBFFT_ONLY_##L(put(generic_entry<Cfg<L, E, S, R0, R1, R2, R3, MINB, PIPE, TC, XB, CH>>(V));)
     GBFFT_GENERIC_SCHEDULES(GBFFT_GX)
 #undef GBFFT_GX
-#define GBFFT_SX(L, V, W, U) GBFFT_ONLY_##L(put(small_entry<SmallCfg<L, W, U>>(V));)
+#define GBFFT_SX(L, V, W, U, CH) GBFFT_ONLY_##L(put(small_entry<SmallCfg<L, W, U, CH>>(V));)
     GBFFT_SMALL_SCHEDULES(GBFFT_SX)
 #undef GBFFT_SX
     return count;

@@ -15,7 +15,9 @@
 //           16 x 16 complex product on FP16 / BF16 tensor cores (tcgen05),
 //           FP32 accumulation, per-signal power-of-two prescale,
 //      XB = exchange buffers: 0 = automatic, 1 = one buffer and two barriers
-//           per exchange (less shared memory, more resident blocks))
+//           per exchange (less shared memory, more resident blocks),
+//      CH = cache hints: bit 0 plain loads, bit 1 plain stores (else
+//           evict-first); the defaults are the measured best per length)
 // Threads per block = S * N / E.  Stage 0 with R0 = E/2 (and the last stage,
 // where its radix is E/2 or less) lets a thread own neighbouring butterflies,
 // so its HBM accesses are 128-bit.  An index model on the host checked the
@@ -23,56 +25,56 @@
 // swizzle of fft_device.cuh (64-bit accesses resolve per half-warp).
 //
 // One-thread-per-signal rows (N <= 32): SX(log2N, variant, warps per block,
-// 32-signal groups per warp tile).
+// 32-signal groups per warp tile, cache hints as CH above).
 #pragma once
 
 #define GBFFT_GENERIC_SCHEDULES(GX)                   \
-    GX(5, 1, 16, 128, 8, 4, 0, 0, 1, 0, 0, 0) \
-    GX(6, 0, 16, 64, 8, 8, 0, 0, 1, 0, 0, 0) \
-    GX(7, 0, 16, 32, 8, 16, 0, 0, 1, 0, 0, 0) \
-    GX(7, 1, 16, 16, 8, 16, 0, 0, 3, 2, 1, 0) \
-    GX(7, 2, 16, 16, 8, 16, 0, 0, 3, 2, 2, 0) \
-    GX(7, 3, 16, 32, 8, 16, 0, 0, 2, 0, 1, 0) \
-    GX(7, 4, 16, 32, 8, 16, 0, 0, 2, 0, 2, 0) \
-    GX(8, 0, 16, 16, 16, 16, 0, 0, 1, 0, 0, 0) \
-    GX(8, 1, 16, 8, 16, 16, 0, 0, 3, 2, 1, 0) \
-    GX(8, 2, 16, 8, 16, 16, 0, 0, 3, 2, 2, 0) \
-    GX(8, 3, 16, 16, 16, 16, 0, 0, 1, 0, 1, 0) \
-    GX(8, 4, 16, 16, 16, 16, 0, 0, 1, 0, 2, 0) \
-    GX(9, 0, 16, 8, 8, 8, 8, 0, 2, 0, 0, 0) \
-    GX(9, 1, 16, 8, 8, 8, 8, 0, 1, 0, 0, 0) \
-    GX(10, 0, 16, 2, 8, 16, 8, 0, 2, 2, 0, 0) \
-    GX(10, 1, 16, 2, 8, 16, 8, 0, 1, 0, 0, 0) \
-    GX(10, 2, 16, 2, 8, 16, 8, 0, 4, 0, 0, 0) \
-    GX(10, 3, 16, 2, 8, 16, 8, 0, 2, 3, 0, 0) \
-    GX(10, 4, 16, 2, 8, 16, 8, 0, 4, 2, 1, 1) \
-    GX(10, 5, 16, 2, 8, 16, 8, 0, 4, 2, 2, 1) \
-    GX(10, 6, 16, 2, 8, 16, 8, 0, 2, 2, 1, 0) \
-    GX(10, 7, 16, 2, 8, 16, 8, 0, 2, 2, 2, 0) \
-    GX(11, 0, 16, 1, 8, 16, 16, 0, 3, 2, 0, 0) \
-    GX(11, 1, 16, 1, 8, 16, 16, 0, 1, 0, 0, 0) \
-    GX(11, 2, 16, 1, 8, 16, 16, 0, 2, 3, 0, 0) \
-    GX(11, 3, 16, 2, 8, 16, 16, 0, 1, 2, 0, 0) \
-    GX(11, 4, 16, 1, 8, 16, 16, 0, 4, 2, 1, 1) \
-    GX(11, 5, 16, 1, 8, 16, 16, 0, 4, 2, 2, 1) \
-    GX(11, 6, 16, 1, 8, 16, 16, 0, 3, 2, 1, 0) \
-    GX(11, 7, 16, 1, 8, 16, 16, 0, 3, 2, 2, 0)
+    GX(5, 1, 16, 128, 8, 4, 0, 0, 1, 0, 0, 0, 0) \
+    GX(6, 0, 16, 64, 8, 8, 0, 0, 1, 0, 0, 0, 0) \
+    GX(7, 0, 16, 32, 8, 16, 0, 0, 1, 0, 0, 0, 2) \
+    GX(7, 1, 16, 16, 8, 16, 0, 0, 3, 2, 1, 0, 0) \
+    GX(7, 2, 16, 16, 8, 16, 0, 0, 3, 2, 2, 0, 0) \
+    GX(7, 3, 16, 32, 8, 16, 0, 0, 2, 0, 1, 0, 0) \
+    GX(7, 4, 16, 32, 8, 16, 0, 0, 2, 0, 2, 0, 0) \
+    GX(8, 0, 16, 16, 16, 16, 0, 0, 1, 0, 0, 0, 2) \
+    GX(8, 1, 16, 8, 16, 16, 0, 0, 3, 2, 1, 0, 0) \
+    GX(8, 2, 16, 8, 16, 16, 0, 0, 3, 2, 2, 0, 0) \
+    GX(8, 3, 16, 16, 16, 16, 0, 0, 1, 0, 1, 0, 0) \
+    GX(8, 4, 16, 16, 16, 16, 0, 0, 1, 0, 2, 0, 0) \
+    GX(9, 0, 16, 8, 8, 8, 8, 0, 2, 0, 0, 0, 3) \
+    GX(9, 1, 16, 8, 8, 8, 8, 0, 1, 0, 0, 0, 0) \
+    GX(10, 0, 16, 2, 8, 16, 8, 0, 2, 2, 0, 0, 2) \
+    GX(10, 1, 16, 2, 8, 16, 8, 0, 1, 0, 0, 0, 0) \
+    GX(10, 2, 16, 2, 8, 16, 8, 0, 4, 0, 0, 0, 0) \
+    GX(10, 3, 16, 2, 8, 16, 8, 0, 2, 3, 0, 0, 0) \
+    GX(10, 4, 16, 2, 8, 16, 8, 0, 4, 2, 1, 1, 0) \
+    GX(10, 5, 16, 2, 8, 16, 8, 0, 4, 2, 2, 1, 0) \
+    GX(10, 6, 16, 2, 8, 16, 8, 0, 2, 2, 1, 0, 0) \
+    GX(10, 7, 16, 2, 8, 16, 8, 0, 2, 2, 2, 0, 0) \
+    GX(11, 0, 16, 1, 8, 16, 16, 0, 3, 2, 0, 0, 2) \
+    GX(11, 1, 16, 1, 8, 16, 16, 0, 1, 0, 0, 0, 0) \
+    GX(11, 2, 16, 1, 8, 16, 16, 0, 2, 3, 0, 0, 0) \
+    GX(11, 3, 16, 2, 8, 16, 16, 0, 1, 2, 0, 0, 0) \
+    GX(11, 4, 16, 1, 8, 16, 16, 0, 4, 2, 1, 1, 0) \
+    GX(11, 5, 16, 1, 8, 16, 16, 0, 4, 2, 2, 1, 0) \
+    GX(11, 6, 16, 1, 8, 16, 16, 0, 3, 2, 1, 0, 0) \
+    GX(11, 7, 16, 1, 8, 16, 16, 0, 3, 2, 2, 0, 0)
 
 #define GBFFT_SMALL_SCHEDULES(SX) \
-    SX(1, 0, 8, 1)                \
-    SX(1, 1, 8, 2)                \
-    SX(2, 0, 8, 4)                \
-    SX(2, 1, 8, 1)                \
-    SX(2, 2, 8, 2)                \
-    SX(2, 3, 4, 4)                \
-    SX(3, 0, 8, 4)                \
-    SX(3, 1, 8, 1)                \
-    SX(3, 2, 4, 4)                \
-    SX(4, 0, 4, 2)                \
-    SX(4, 1, 8, 1)                \
-    SX(4, 2, 8, 2)                \
-    SX(5, 0, 2, 2)                \
-    SX(5, 2, 4, 1)
+    SX(1, 0, 8, 1, 3)                \
+    SX(1, 1, 8, 2, 0)                \
+    SX(2, 0, 8, 4, 2)                \
+    SX(2, 1, 8, 1, 0)                \
+    SX(2, 2, 8, 2, 0)                \
+    SX(2, 3, 4, 4, 0)                \
+    SX(3, 0, 8, 4, 0)                \
+    SX(3, 1, 8, 1, 0)                \
+    SX(3, 2, 4, 4, 0)                \
+    SX(4, 0, 4, 2, 2)                \
+    SX(4, 1, 8, 1, 0)                \
+    SX(4, 2, 8, 2, 0)                \
+    SX(5, 0, 2, 2, 0)                \
+    SX(5, 2, 4, 1, 0)
 
 #define GBFFT_MIN_LOG2N 1
 #define GBFFT_MAX_LOG2N 11
