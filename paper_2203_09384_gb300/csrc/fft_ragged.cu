@@ -46,6 +46,8 @@ struct RaggedArgs {
     const float2* tw;
     int tw_off[GBFFT_MAX_LOG2N + 1];
     unsigned int* counter;
+    int* err;          // device error word (bounded waits of the prefetch ring)
+    uint64_t wait_ns;  // limit of each such wait
 };
 
 // per-variant, per-length schedules; every one has 256 threads per block
@@ -83,15 +85,27 @@ GBFFT_RCFG(1, 10, 8, 2, 4, 4, 8, 8)
 GBFFT_RCFG(1, 11, 8, 1, 4, 8, 8, 8)
 #undef GBFFT_RCFG
 
-constexpr int kRaggedVariants = 2;
+// variants 0..3: bit 0 schedule set, bit 1 work distribution; variant 4: the
+// schedule set 1 shapes fed by a bulk-copy (TMA) prefetch ring
+constexpr int kRaggedVariants = 5;
+constexpr int kRingVariant = 4;
+
+// the ring variant's per-length schedules: set 1 with a 2-slot ring
+template <int L>
+struct RingCfg {
+    using B = typename RCfg<1, L>::type;
+    using type = Cfg<L, B::E, B::S, B::radix(0), B::radix(1), B::radix(2), B::radix(3), 3, 2>;
+};
+constexpr int kRingTile = 2048;  // complex elements per item (S * N) at most
 constexpr int kRaggedThreads = 256;
 template <int V>
 struct RaggedMinBlocks {
     static constexpr int value = V == 0 ? 2 : 3;
 };
 
-template <int V>
+template <int V0>
 constexpr int ragged_smem_bytes() {
+    constexpr int V = V0 & 1;
     int m = 0;
 #define GBFFT_RSMEM(L) m = m > RCfg<V, L>::type::kSmemElems * 8 ? m : RCfg<V, L>::type::kSmemElems * 8;
     GBFFT_RSMEM(1) GBFFT_RSMEM(2) GBFFT_RSMEM(3) GBFFT_RSMEM(4) GBFFT_RSMEM(5) GBFFT_RSMEM(6)
@@ -100,13 +114,19 @@ constexpr int ragged_smem_bytes() {
     return m;
 }
 
+// Offset of this thread's signal in work item w (0 when the thread has none).
+template <class C>
+__device__ __forceinline__ int64_t ragged_offset(const RaggedArgs& a, const RaggedItem& w) {
+    const int sl = threadIdx.x / C::T;
+    return sl < w.count ? a.sig_off[w.first + sl] : 0;
+}
+
 template <class C, bool INV>
-__device__ __forceinline__ void ragged_tile(const RaggedArgs& a, const RaggedItem& w, float2* smem) {
+__device__ __forceinline__ void ragged_tile(const RaggedArgs& a, const RaggedItem& w, float2* smem, int64_t off) {
     const int tid = threadIdx.x;
     const int sl = tid / C::T;
     const int t = tid % C::T;
     const bool active = sl < w.count;
-    const int64_t off = active ? a.sig_off[w.first + sl] : 0;
     const float2* tw = a.tw + a.tw_off[C::LOG2N];
     const float scale = a.scale_mode ? 1.0f / (float)C::N : 1.0f;
     int buf = 0;
@@ -118,25 +138,157 @@ __device__ __forceinline__ void ragged_tile(const RaggedArgs& a, const RaggedIte
     store_last<C, INV>(v, a.out + off, t, active, scale);
 }
 
+template <int V>
+__device__ __forceinline__ int64_t ragged_offset_for(const RaggedArgs& a, const RaggedItem& w) {
+    switch (w.log2n) {
+#define GBFFT_ROFF(L) \
+    case L: return ragged_offset<typename RCfg<V, L>::type>(a, w);
+        GBFFT_ROFF(1) GBFFT_ROFF(2) GBFFT_ROFF(3) GBFFT_ROFF(4) GBFFT_ROFF(5) GBFFT_ROFF(6)
+        GBFFT_ROFF(7) GBFFT_ROFF(8) GBFFT_ROFF(9) GBFFT_ROFF(10) GBFFT_ROFF(11)
+#undef GBFFT_ROFF
+        default: return 0;
+    }
+}
+
 template <int V, bool INV>
-__global__ void __launch_bounds__(kRaggedThreads, RaggedMinBlocks<V>::value) fft_ragged_kernel(RaggedArgs a) {
-    extern __shared__ __align__(16) float2 smem[];
-    __shared__ int s_item;
-    for (;;) {
-        if (threadIdx.x == 0) s_item = (int)atomicAdd(a.counter, 1u);
-        __syncthreads();
-        const int it = s_item;
-        __syncthreads();  // everyone has read s_item before the next fetch
-        if (it >= a.n_items) break;
-        const RaggedItem w = a.items[it];
-        switch (w.log2n) {
+__device__ __forceinline__ void ragged_dispatch(const RaggedArgs& a, const RaggedItem& w, float2* smem, int64_t off) {
+    switch (w.log2n) {
 #define GBFFT_RCASE(L) \
-    case L: ragged_tile<typename RCfg<V, L>::type, INV>(a, w, smem); break;
-            GBFFT_RCASE(1) GBFFT_RCASE(2) GBFFT_RCASE(3) GBFFT_RCASE(4) GBFFT_RCASE(5) GBFFT_RCASE(6)
-            GBFFT_RCASE(7) GBFFT_RCASE(8) GBFFT_RCASE(9) GBFFT_RCASE(10) GBFFT_RCASE(11)
+    case L: ragged_tile<typename RCfg<V, L>::type, INV>(a, w, smem, off); break;
+        GBFFT_RCASE(1) GBFFT_RCASE(2) GBFFT_RCASE(3) GBFFT_RCASE(4) GBFFT_RCASE(5) GBFFT_RCASE(6)
+        GBFFT_RCASE(7) GBFFT_RCASE(8) GBFFT_RCASE(9) GBFFT_RCASE(10) GBFFT_RCASE(11)
 #undef GBFFT_RCASE
+        default: break;
+    }
+}
+
+// Variant bit 1 selects how blocks get work: 0 = the shared counter (each
+// block takes the next item with one atomicAdd), 1 = static round robin
+// (block b takes items b, b + grid, ...) with the next item's descriptor and
+// this thread's signal offset loaded while the current item is transformed,
+// so the data loads of an item start without a chain of dependent reads.
+template <int V, bool INV>
+__global__ void __launch_bounds__(kRaggedThreads, RaggedMinBlocks<V & 1>::value) fft_ragged_kernel(RaggedArgs a) {
+    constexpr int S = V & 1;  // schedule set
+    extern __shared__ __align__(16) float2 smem[];
+    if constexpr ((V >> 1) == 0) {
+        __shared__ int s_item;
+        for (;;) {
+            if (threadIdx.x == 0) s_item = (int)atomicAdd(a.counter, 1u);
+            __syncthreads();
+            const int it = s_item;
+            __syncthreads();  // everyone has read s_item before the next fetch
+            if (it >= a.n_items) break;
+            const RaggedItem w = a.items[it];
+            ragged_dispatch<S, INV>(a, w, smem, ragged_offset_for<S>(a, w));
+        }
+    } else {
+        int it = blockIdx.x;
+        if (it >= a.n_items) return;
+        RaggedItem w = a.items[it];
+        int64_t off = ragged_offset_for<S>(a, w);
+        for (;;) {
+            const int nx = it + (int)gridDim.x;
+            RaggedItem wn{};
+            int64_t offn = 0;
+            if (nx < a.n_items) {  // prefetch the next item's descriptor and offset
+                wn = a.items[nx];
+                offn = ragged_offset_for<S>(a, wn);
+            }
+            ragged_dispatch<S, INV>(a, w, smem, off);
+            if (nx >= a.n_items) break;
+            __syncthreads();  // the next item may reuse shared memory differently
+            it = nx;
+            w = wn;
+            off = offn;
+        }
+    }
+}
+
+// Warp 0 copies every signal of item `it` into ring slot `slot`: one bulk copy
+// per signal (contiguous in HBM), all completing on the slot's mbarrier.
+__device__ __forceinline__ void ragged_issue(const RaggedArgs& a, float2* slot_base, uint64_t* bar, int it) {
+    const int lane = threadIdx.x & 31;
+    const RaggedItem w = a.items[it];
+    const int n = 1 << w.log2n;
+    if (lane == 0) mbar_arrive_expect_tx(bar, (uint32_t)(w.count * n * 8));
+    __syncwarp();
+    for (int k = lane; k < w.count; k += 32)
+        bulk_copy_g2s(slot_base + k * n, a.in + a.sig_off[w.first + k], (uint32_t)(n * 8), bar);
+}
+
+template <class C, bool INV>
+__device__ __forceinline__ void ragged_ring_tile(const RaggedArgs& a, const RaggedItem& w, float2* xbuf,
+                                                 const float2* slot_base, int64_t off, bool dead,
+                                                 float2* refill_base, uint64_t* refill_bar, int refill_it) {
+    const int tid = threadIdx.x;
+    const int sl = tid / C::T;
+    const int t = tid % C::T;
+    const bool active = sl < w.count && !dead;
+    const float2* tw = a.tw + a.tw_off[C::LOG2N];
+    const float scale = a.scale_mode ? 1.0f / (float)C::N : 1.0f;
+    TcCtx tc;
+    float2 v[C::E];
+    gather_tile<C, INV>(v, slot_base, sl * C::N, t);
+    __syncthreads();  // every thread has read the slot: refill it
+    if (tid < 32 && refill_it >= 0) {
+        fence_proxy_async_smem();
+        ragged_issue(a, refill_base, refill_bar, refill_it);
+    }
+    int buf = 0;
+    twist_and_dft<C, 0>(v, t, tw, tc);
+    rest_stages<C, 1>(v, xbuf, buf, sl * C::N, t, tw, tc);
+    store_last<C, INV>(v, a.out + off, t, active, scale);
+}
+
+// Static round robin over the work list; warp 0 keeps the next item's
+// signals in flight into the other ring slot while the current one runs.
+template <bool INV>
+__global__ void __launch_bounds__(kRaggedThreads, 3) fft_ragged_ring_kernel(RaggedArgs a) {
+    extern __shared__ __align__(16) float2 smem[];
+    float2* xbuf = smem;                   // 2 exchange buffers
+    float2* ring = smem + 2 * kRingTile;   // 2 ring slots
+    uint64_t* bars = reinterpret_cast<uint64_t*>(ring + 2 * kRingTile);
+    const int tid = threadIdx.x;
+    const int grid = (int)gridDim.x;
+    if (tid == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (tid < 32) {
+        for (int d = 0; d < 2; ++d) {
+            const int it = (int)blockIdx.x + d * grid;
+            if (it < a.n_items) ragged_issue(a, ring + d * kRingTile, &bars[d], it);
+        }
+    }
+    bool dead = false;
+    int k = 0;
+    for (int it = blockIdx.x; it < a.n_items; it += grid, ++k) {
+        const int slot = k & 1;
+        const uint32_t parity = (uint32_t)((k >> 1) & 1);
+        if (!dead && !mbar_wait_bounded(&bars[slot], parity, a.wait_ns)) {
+            dead = true;
+            atomicCAS(a.err, 0, kErrTimeout);
+        }
+        const RaggedItem w = a.items[it];
+        const int nx = it + 2 * grid;
+        const int refill = (nx < a.n_items && !dead) ? nx : -1;
+        switch (w.log2n) {
+#define GBFFT_RRING(L)                                                                                        \
+    case L: {                                                                                                 \
+        using C = typename RingCfg<L>::type;                                                                  \
+        ragged_ring_tile<C, INV>(a, w, xbuf, ring + slot * kRingTile, ragged_offset<C>(a, w), dead,           \
+                                 ring + slot * kRingTile, &bars[slot], refill);                               \
+        break;                                                                                                \
+    }
+            GBFFT_RRING(1) GBFFT_RRING(2) GBFFT_RRING(3) GBFFT_RRING(4) GBFFT_RRING(5) GBFFT_RRING(6)
+            GBFFT_RRING(7) GBFFT_RRING(8) GBFFT_RRING(9) GBFFT_RRING(10) GBFFT_RRING(11)
+#undef GBFFT_RRING
             default: break;
         }
+        __syncthreads();  // the next item reuses shared memory with another shape
     }
 }
 
@@ -145,8 +297,9 @@ __global__ void __launch_bounds__(kRaggedThreads, RaggedMinBlocks<V>::value) fft
 // ---------------------------------------------------------------------------
 namespace {
 
-template <int V>
+template <int V0>
 struct RaggedHost {
+    static constexpr int V = V0 & 1;  // schedule set
     static int signals_per_tile(int L) {
         switch (L) {
 #define GBFFT_RS(L) \
@@ -189,21 +342,42 @@ struct RaggedHost {
         }
     }
     static const void* kernel(bool inv) {
-        return inv ? reinterpret_cast<const void*>(&fft_ragged_kernel<V, true>)
-                   : reinterpret_cast<const void*>(&fft_ragged_kernel<V, false>);
+        return inv ? reinterpret_cast<const void*>(&fft_ragged_kernel<V0, true>)
+                   : reinterpret_cast<const void*>(&fft_ragged_kernel<V0, false>);
     }
 };
 
-int signals_per_tile(int v, int L) { return v == 0 ? RaggedHost<0>::signals_per_tile(L) : RaggedHost<1>::signals_per_tile(L); }
-int twiddle_count(int v, int L) { return v == 0 ? RaggedHost<0>::twiddles(L) : RaggedHost<1>::twiddles(L); }
+// The schedule set a variant's kernel runs: bit 0 of variants 0..3; the ring
+// variant runs set 1.  Work list, tile sizes and twiddle tables must follow it.
+int schedule_set(int v) { return v == kRingVariant ? 1 : (v & 1); }
+
+int signals_per_tile(int v, int L) {
+    return schedule_set(v) == 0 ? RaggedHost<0>::signals_per_tile(L) : RaggedHost<1>::signals_per_tile(L);
+}
+int twiddle_count(int v, int L) {
+    return schedule_set(v) == 0 ? RaggedHost<0>::twiddles(L) : RaggedHost<1>::twiddles(L);
+}
 void fill_twiddles(int v, int L, float* host) {
-    if (v == 0)
+    if (schedule_set(v) == 0)
         RaggedHost<0>::fill_twiddles(L, host);
     else
         RaggedHost<1>::fill_twiddles(L, host);
 }
-const void* ragged_kernel(int v, bool inv) { return v == 0 ? RaggedHost<0>::kernel(inv) : RaggedHost<1>::kernel(inv); }
-int ragged_smem(int v) { return v == 0 ? ragged_smem_bytes<0>() : ragged_smem_bytes<1>(); }
+const void* ragged_kernel(int v, bool inv) {
+    switch (v) {
+        case 0: return RaggedHost<0>::kernel(inv);
+        case 1: return RaggedHost<1>::kernel(inv);
+        case 2: return RaggedHost<2>::kernel(inv);
+        case 3: return RaggedHost<3>::kernel(inv);
+        default:
+            return inv ? reinterpret_cast<const void*>(&fft_ragged_ring_kernel<true>)
+                       : reinterpret_cast<const void*>(&fft_ragged_ring_kernel<false>);
+    }
+}
+int ragged_smem(int v) {
+    if (v == kRingVariant) return 4 * kRingTile * (int)sizeof(float2) + 16;
+    return schedule_set(v) == 0 ? ragged_smem_bytes<0>() : ragged_smem_bytes<1>();
+}
 
 }  // namespace
 
@@ -260,6 +434,10 @@ fft_status_t ragged_create(const int64_t* offsets, int64_t count, int direction,
         tw_off[L] = tw_total;
         tw_total += twiddle_count(variant, L);
         const int S = signals_per_tile(variant, L);
+        if (S < 1 || (variant == kRingVariant && (int64_t)S << L > kRingTile)) {  // a tile must fit the kernel
+            delete st;
+            return FFT_ERR_UNSUPPORTED;
+        }
         for (size_t k = 0; k < buckets[L].size(); k += S) {
             RaggedItem it;
             it.log2n = L;
@@ -301,6 +479,8 @@ fft_status_t ragged_create(const int64_t* offsets, int64_t count, int direction,
     st->args.tw = reinterpret_cast<const float2*>(base + off_tw);
     for (int L = 0; L <= GBFFT_MAX_LOG2N; ++L) st->args.tw_off[L] = tw_off[L];
     st->args.scale_mode = st->scale_mode;
+    st->args.err = reinterpret_cast<int*>(base + 16);
+    st->args.wait_ns = 4000000000ull;
 
     // launch shape: persistent, every SM filled
     const void* k = ragged_kernel(variant, st->inverse);
@@ -357,9 +537,11 @@ void ragged_info(const RaggedState* st, fft_plan_info_t* info) {
     info->grid = st->grid;
     info->kernel_kind = 3;
     info->num_stages = 0;
-    info->elems_per_thread = st->variant == 0 ? 16 : 8;
+    info->elems_per_thread = schedule_set(st->variant) == 0 ? 16 : 8;
     info->work_items = st->n_items;
 }
+
+int* ragged_error_word(RaggedState* st) { return st->args.err; }
 
 void ragged_destroy(RaggedState* st) {
     if (!st) return;

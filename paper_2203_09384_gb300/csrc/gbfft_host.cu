@@ -450,6 +450,7 @@ fft_status_t fft_plan_create_ragged(const int64_t* offsets_host, int64_t count, 
     p->flags = flags;
     p->device = dev;
     p->grid = grid;
+    p->d_error = gbfft::ragged_error_word(p->ragged);
     *plan = p;
     return FFT_OK;
 }

@@ -45,6 +45,7 @@ fft_status_t ragged_create(const int64_t* offsets, int64_t count, int direction,
                            RaggedState** out, int64_t* grid_out);
 fft_status_t ragged_execute(RaggedState* st, const void* in, void* out, void* stream);
 void ragged_info(const RaggedState* st, fft_plan_info_t* info);
+int* ragged_error_word(RaggedState* st);
 void ragged_destroy(RaggedState* st);
 
 }  // namespace gbfft

@@ -49,7 +49,7 @@ def workload():
     return offsets.numpy(), x, want
 
 
-@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("variant", list(range(gb.fft_ragged_variant_count())))
 def test_ragged_workload_in_a_cuda_graph(workload, variant):
     offsets, x, want = workload
     xd = x.cuda()
@@ -64,6 +64,7 @@ def test_ragged_workload_in_a_cuda_graph(workload, variant):
     torch.cuda.synchronize()
     got = out.cpu().numpy().astype(np.complex128)
     assert per_signal_max_err(got, want, offsets) <= FP32_TOL
+    assert _abi.lib().fft_plan_get_error(plan.handle) == 0
     plan.close()
 
 
