@@ -63,10 +63,10 @@
 #define GBFFT_SMALL_SCHEDULES(SX) \
     SX(1, 0, 8, 1, 3)                \
     SX(1, 1, 8, 2, 0)                \
-    SX(2, 0, 8, 4, 2)                \
+    SX(2, 0, 4, 8, 2)                \
     SX(2, 1, 8, 1, 0)                \
-    SX(2, 2, 8, 2, 0)                \
-    SX(2, 3, 4, 4, 0)                \
+    SX(2, 2, 8, 4, 2)                \
+    SX(2, 3, 16, 2, 2)               \
     SX(3, 0, 8, 4, 0)                \
     SX(3, 1, 8, 1, 0)                \
     SX(3, 2, 4, 4, 0)                \
