@@ -46,11 +46,14 @@ enum {
     FFT_INVERSE = 1  /* Eq. (idft): exponent sign +1, times 1/N (unless flagged) */
 };
 
-/* Arithmetic type of the transform.  Input and output are complex64 for all. */
+/* Arithmetic / storage type.  Input and output are complex64 except FFT_C32. */
 enum {
     FFT_C64 = 0,         /* FP32 arithmetic throughout                          */
     FFT_C64_TC_F16 = 1,  /* radix-16 stages on FP16 tensor cores, FP32 accumulate */
-    FFT_C64_TC_BF16 = 2  /* radix-16 stages on BF16 tensor cores, FP32 accumulate */
+    FFT_C64_TC_BF16 = 2, /* radix-16 stages on BF16 tensor cores, FP32 accumulate */
+    FFT_C32 = 3          /* complex32 STORAGE (two binary16 per element, with a
+                            per-signal power-of-two exponent), FP32 arithmetic;
+                            run with fft_execute_c32                           */
 };
 
 /* Plan flags (fft_plan_create_ex). */
@@ -144,6 +147,22 @@ GBFFT_API fft_status_t fft_plan_create_ex(int64_t n, int64_t batch, int directio
 GBFFT_API fft_status_t fft_execute(fft_plan_t plan, const void* in, void* out, void* stream);
 
 /*
+ * The planned transform for complex32 storage (plan dtype FFT_C32): `in` and
+ * `out` hold batch*n elements of two IEEE binary16 each (re, im; 4 bytes),
+ * signal b meaning stored * 2^in_exp[b] (input) and stored * 2^out_exp[b]
+ * (output).  in_exp / out_exp are device arrays of `batch` int8.  The
+ * arithmetic is FP32; the call picks out_exp[b] so that the signal's largest
+ * output component lands in [2^14, 2^15) (the binary16 range, full
+ * precision).  Half the HBM bytes of complex64 for about 2^-11 relative
+ * storage rounding.  Pointers 16-byte aligned (exponent arrays any
+ * alignment); in == out allowed; asynchronous on `stream` like fft_execute.
+ * Errors: FFT_ERR_INVALID_VALUE (NULL, or the plan is not FFT_C32),
+ * FFT_ERR_MISALIGNED, FFT_ERR_OVERLAP, FFT_ERR_CUDA.
+ */
+GBFFT_API fft_status_t fft_execute_c32(fft_plan_t plan, const void* in, const int8_t* in_exp, void* out,
+                                       int8_t* out_exp, void* stream);
+
+/*
  * The planned transform on HOST buffers: batch*n complex64 read from
  * `in_host`, results written to `out_host` (equal, or not overlapping).  The
  * plan must have been made with FFT_FLAG_HOST_STAGING.  Work is split into
@@ -188,7 +207,7 @@ typedef struct {
     int pipeline;           /* bulk-copy (TMA) prefetch ring depth, 0 = none     */
     int min_blocks;         /* launch-bounds residency hint                     */
     int kernel_kind;        /* 0 one thread per signal, 1 direct, 2 TMA ring,
-                               3 ragged persistent work list                    */
+                               3 ragged persistent work list, 4 complex32 I/O   */
     int64_t work_items;     /* ragged plans: tiles in the device work list      */
     int tc;                 /* radix-16 stages on tensor cores: 0 no (FP32),
                                1 FP16 operands, 2 BF16 operands                 */
@@ -210,7 +229,7 @@ GBFFT_API fft_status_t fft_plan_get_info(fft_plan_t plan, fft_plan_info_t* info)
 GBFFT_API int fft_variant_count(int64_t n);
 GBFFT_API fft_status_t fft_set_default_variant(int64_t n, int variant);
 GBFFT_API int fft_get_default_variant(int64_t n);
-/* The dtype (FFT_C64, FFT_C64_TC_F16 or FFT_C64_TC_BF16) that variant k of
+/* The dtype (FFT_C64, FFT_C64_TC_F16, FFT_C64_TC_BF16 or FFT_C32) that variant k of
  * length n computes in, or -1 when there is no such variant.  Plans accept a
  * variant only with its own dtype. */
 GBFFT_API int fft_variant_dtype(int64_t n, int variant);

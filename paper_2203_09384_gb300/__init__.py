@@ -16,7 +16,8 @@ import threading
 
 import torch
 
-from ._abi import (FFT_C64, FFT_C64_TC_BF16, FFT_C64_TC_F16, FFT_FLAG_SCALE_FORWARD,  # noqa: F401
+from ._abi import (FFT_C32, FFT_C64, FFT_C64_TC_BF16, FFT_C64_TC_F16, FFT_FLAG_SCALE_FORWARD,  # noqa: F401
+                   fft_execute_c32,
                    FFT_FLAG_UNNORMALIZED, FFT_FLAG_VARIANT, fft_get_default_variant,
                    fft_plan_create_ragged, fft_ragged_variant_count, fft_variant_dtype,
                    DTYPE_NAMES,
@@ -31,7 +32,7 @@ __all__ = ["Plan", "RaggedPlan", "fft", "ifft", "FFTFunction", "IFFTFunction", "
            "fft_plan_create_ex", "fft_plan_create_ragged", "fft_execute", "fft_plan_destroy",
            "fft_plan_get_error", "FFTError", "lib"]
 
-_DTYPES = {"c64": FFT_C64, "tc_f16": FFT_C64_TC_F16, "tc_bf16": FFT_C64_TC_BF16}
+_DTYPES = {"c64": FFT_C64, "tc_f16": FFT_C64_TC_F16, "tc_bf16": FFT_C64_TC_BF16, "c32": FFT_C32}
 
 
 class Plan:
@@ -81,6 +82,27 @@ class Plan:
             s = stream if stream is not None else torch.cuda.current_stream(x.device)
             fft_execute(self.handle, x.data_ptr(), out.data_ptr(), s.cuda_stream)
         return out
+
+    def execute_c32(self, x: torch.Tensor, x_exp: torch.Tensor, out: torch.Tensor | None = None,
+                    out_exp: torch.Tensor | None = None, stream=None):
+        """complex32 storage (plan dtype "c32"): x is a torch.complex32 CUDA
+        tensor, x_exp an int8 tensor of one exponent per signal (value =
+        stored * 2^exp).  Returns (out, out_exp) in the same representation."""
+        if x.dtype != torch.complex32 or not x.is_cuda or not x.is_contiguous():
+            raise TypeError("expected a contiguous complex32 CUDA tensor")
+        if x.numel() != self.n * self.batch or x_exp.numel() != self.batch or x_exp.dtype != torch.int8:
+            raise ValueError("shape mismatch: x needs n*batch elements, x_exp batch int8")
+        if out is None:
+            out = torch.empty_like(x)
+        elif out.dtype != torch.complex32 or not out.is_contiguous() or out.numel() != x.numel():
+            raise ValueError("out must be a contiguous complex32 tensor like x")
+        if out_exp is None:
+            out_exp = torch.empty(self.batch, dtype=torch.int8, device=x.device)
+        with torch.cuda.device(x.device):
+            s = stream if stream is not None else torch.cuda.current_stream(x.device)
+            fft_execute_c32(self.handle, x.data_ptr(), x_exp.contiguous().data_ptr(), out.data_ptr(),
+                            out_exp.data_ptr(), s.cuda_stream)
+        return out, out_exp
 
     def execute_host(self, x: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
         """Transform a host (CPU, ideally pinned) tensor through the plan's

@@ -18,6 +18,7 @@ FFT_INVERSE = 1
 FFT_C64 = 0
 FFT_C64_TC_F16 = 1
 FFT_C64_TC_BF16 = 2
+FFT_C32 = 3
 FFT_FLAG_UNNORMALIZED = 1 << 0
 FFT_FLAG_SCALE_FORWARD = 1 << 1
 FFT_FLAG_VARIANT_MASK = 0xF << 8
@@ -115,6 +116,8 @@ def lib() -> ctypes.CDLL:
     L.fft_plan_create.argtypes = [_i64, _i64, _int, _int, ctypes.POINTER(_vp)]
     L.fft_plan_create_ex.restype = _int
     L.fft_plan_create_ex.argtypes = [_i64, _i64, _int, _int, _u32, ctypes.POINTER(_vp)]
+    L.fft_execute_c32.restype = _int
+    L.fft_execute_c32.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp]
     L.fft_execute_host.restype = _int
     L.fft_execute_host.argtypes = [_vp, _vp, _vp, _vp]
     L.fft_execute.restype = _int
@@ -234,7 +237,7 @@ def fft_ragged_variant_count() -> int:
     return lib().fft_ragged_variant_count()
 
 
-DTYPE_NAMES = {FFT_C64: "c64", FFT_C64_TC_F16: "tc_f16", FFT_C64_TC_BF16: "tc_bf16"}
+DTYPE_NAMES = {FFT_C64: "c64", FFT_C64_TC_F16: "tc_f16", FFT_C64_TC_BF16: "tc_bf16", FFT_C32: "c32"}
 
 
 def fft_variant_dtype(n: int, variant: int) -> int:
@@ -243,3 +246,8 @@ def fft_variant_dtype(n: int, variant: int) -> int:
 
 def fft_execute_host(plan: int, in_host: int, out_host: int, stream: int = 0) -> None:
     check(lib().fft_execute_host(plan, in_host, out_host, stream), "fft_execute_host")
+
+
+def fft_execute_c32(plan: int, in_ptr: int, in_exp_ptr: int, out_ptr: int, out_exp_ptr: int,
+                    stream: int = 0) -> None:
+    check(lib().fft_execute_c32(plan, in_ptr, in_exp_ptr, out_ptr, out_exp_ptr, stream), "fft_execute_c32")

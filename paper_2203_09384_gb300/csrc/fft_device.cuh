@@ -26,6 +26,7 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <string.h>
 
 namespace gbfft {
 
@@ -913,5 +914,362 @@ __global__ void __launch_bounds__(SC::NT) fft_small_kernel(const float2* in, flo
         __syncwarp();
     }
 }
+
+// ---------------------------------------------------------------------------
+// complex32 storage: each element is two IEEE binary16 (re, im) and signal b
+// carries a power-of-two exponent, value = stored * 2^exp[b].  The transform
+// is linear, so the kernels transform the stored values themselves in FP32
+// (|stored| < 2^16, at most N * 2^16 after the transform) and fold the input
+// exponent and the 1/N normalisation into the output exponent; one
+// power-of-two multiply per component puts each signal's largest output
+// component in [2^14, 2^15).
+// ---------------------------------------------------------------------------
+// binary16 pairs moved as 32-bit words
+__device__ __forceinline__ __half2 bits_h2(float x) {
+    __half2 h;
+    memcpy(&h, &x, 4);
+    return h;
+}
+__device__ __forceinline__ float h2_bits(__half2 h) {
+    float x;
+    memcpy(&x, &h, 4);
+    return x;
+}
+
+struct C32Out {
+    int e;       // output exponent
+    float mult;  // stored output = transform of stored input * mult
+};
+
+// m = largest |component| of the signal's unscaled FP32 transform; the
+// values carry 2^(ein + ls) (input exponent, log2 of the normalisation).
+__device__ __forceinline__ C32Out c32_out_scale(float m, int ein, int ls) {
+    if (!(m > 0.0f) || !(m <= 3.0e38f)) return {0, 1.0f};  // zero (or non-finite) signal
+    int f = 0;
+    frexpf(m, &f);  // m = g 2^f, g in [0.5, 1)
+    int e = ein + ls + f - 15;
+    e = e < -128 ? -128 : (e > 127 ? 127 : e);  // int8: stored values under/overflow past this
+    int k = ein + ls - e;                       // 15 - f unless e was clamped
+    k = k < -126 ? -126 : (k > 127 ? 127 : k);
+    return {e, __int_as_float((k + 127) << 23)};  // 2^k, a normal binary32
+}
+
+// log2 of the power-of-two normalisation factor (1, 1/N)
+__device__ __forceinline__ int log2_pow2(float scale) {
+    int x = 0;
+    frexpf(scale, &x);
+    return x - 1;
+}
+
+template <class C, bool INV>
+__device__ __forceinline__ void load_first_c32(float2 (&v)[C::E], const __half2* src, int t, bool active) {
+    constexpr int R = C::radix(0);
+    constexpr int K = C::E / R;
+    constexpr int stride = C::N / R;
+    if (!active) {
+#pragma unroll
+        for (int i = 0; i < C::E; ++i) v[i] = make_float2(0.f, 0.f);
+        return;
+    }
+    if constexpr (K >= 2) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+#pragma unroll
+            for (int c = 0; c < K; c += 2) {
+                const float2 raw = __ldcs(reinterpret_cast<const float2*>(src + K * t + c + r * stride));
+                v[c * R + r] = __half22float2(bits_h2(raw.x));
+                v[(c + 1) * R + r] = __half22float2(bits_h2(raw.y));
+            }
+        }
+    } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = __half22float2(src[t + r * stride]);
+    }
+    if constexpr (INV) {
+#pragma unroll
+        for (int i = 0; i < C::E; ++i) v[i].y = -v[i].y;
+    }
+}
+
+// Largest |component| of the thread's signal (every thread of the block calls it).
+template <class C>
+__device__ __forceinline__ float c32_signal_max(const float2 (&v)[C::E], float* red) {
+    float m = 0.0f;
+#pragma unroll
+    for (int i = 0; i < C::E; ++i) m = fmaxf(m, fmaxf(fabsf(v[i].x), fabsf(v[i].y)));
+    if constexpr (C::T <= 32) {
+#pragma unroll
+        for (int o = 1; o < C::T; o <<= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    } else {
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        const int warp = threadIdx.x >> 5;
+        if ((threadIdx.x & 31) == 0) red[warp] = m;
+        __syncthreads();
+        constexpr int W = C::T / 32;
+        const int w0 = (warp / W) * W;
+        m = 0.0f;
+#pragma unroll
+        for (int w = 0; w < W; ++w) m = fmaxf(m, red[w0 + w]);
+    }
+    return m;
+}
+
+template <class C, bool INV>
+__device__ __forceinline__ void store_last_c32(const float2 (&v)[C::E], __half2* dst, int8_t* exp_out, int t,
+                                               bool active, C32Out o) {
+    constexpr int R = C::radix(C::M - 1);
+    constexpr int K = C::E / R;
+    constexpr int stride = C::N / R;
+    if (!active) return;
+    if (t == 0) *exp_out = (int8_t)o.e;
+    const float my = INV ? -o.mult : o.mult;
+    if constexpr (K >= 2) {
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+#pragma unroll
+            for (int c = 0; c < K; c += 2) {
+                const float2 raw =
+                    make_float2(h2_bits(__floats2half2_rn(v[c * R + q].x * o.mult, v[c * R + q].y * my)),
+                                h2_bits(__floats2half2_rn(v[(c + 1) * R + q].x * o.mult, v[(c + 1) * R + q].y * my)));
+                __stcs(reinterpret_cast<float2*>(dst + K * t + c + q * stride), raw);
+            }
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < R; ++q) dst[t + q * stride] = __floats2half2_rn(v[q].x * o.mult, v[q].y * my);
+    }
+}
+
+// Shared memory of the complex32 kernels: FP32 exchange buffers, then (ring
+// variants) PIPE binary16 tiles and their mbarriers, then per-warp maxima.
+template <class C>
+struct C32Smem {
+    static constexpr int kRingOffset = C::kSmemElems * 8;
+    static constexpr int kBarOffset = kRingOffset + C::PIPE * C::S * C::N * 4;
+    static constexpr int kRedOffset = kBarOffset + C::PIPE * 8;
+    static constexpr int kBytes = kRedOffset + 128;
+};
+
+// Direct loads.  err / wait_ns / stall are accepted so that all complex32
+// kernels share one argument list; nothing here waits.
+template <class C, bool INV>
+__global__ void __launch_bounds__(C::NT, C::MINB)
+    fft_stockham_c32_kernel(const __half2* in, const int8_t* in_exp, __half2* out, int8_t* out_exp, int64_t batch,
+                            const float2* __restrict__ tw, float scale, int* err, uint64_t wait_ns, int stall) {
+    extern __shared__ __align__(16) float2 smem[];
+    float* red = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(smem) + C32Smem<C>::kRedOffset);
+    const int tid = threadIdx.x;
+    const int sl = tid / C::T;
+    const int t = tid % C::T;
+    const int sb = sl * C::N;
+    const int ls = log2_pow2(scale);
+    const int64_t ntiles = (batch + C::S - 1) / C::S;
+    TcCtx tc;  // FP32 butterflies only
+    int buf = 0;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t sig = tile * C::S + sl;
+        const bool active = sig < batch;
+        const int64_t base = sig * C::N;
+        const int ein = active ? (int)in_exp[sig] : 0;
+        float2 v[C::E];
+        load_first_c32<C, INV>(v, in + base, t, active);
+        twist_and_dft<C, 0>(v, t, tw, tc);
+        rest_stages<C, 1>(v, smem, buf, sb, t, tw, tc);
+        const C32Out o = c32_out_scale(c32_signal_max<C>(v, red), ein, ls);
+        store_last_c32<C, INV>(v, out + base, out_exp + sig, t, active, o);
+    }
+}
+
+// stage-0 inputs of a complex32 signal from its binary16 tile in shared memory
+template <class C, bool INV>
+__device__ __forceinline__ void gather_tile_c32(float2 (&v)[C::E], const __half2* tile, int sb, int t) {
+    constexpr int R = C::radix(0);
+    constexpr int K = C::E / R;
+    constexpr int stride = C::N / R;
+#pragma unroll
+    for (int c = 0; c < K; ++c) {
+        const int j = bfly<C, 0>(t, c);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const float2 a = __half22float2(tile[sb + j + r * stride]);
+            v[c * R + r] = INV ? conj2(a) : a;
+        }
+    }
+}
+
+// complex32 with the bulk-copy ring: thread 0 keeps PIPE binary16 tiles in
+// flight as in fft_stockham_ring_kernel, with the same bounded waits and
+// error word.
+template <class C, bool INV>
+__global__ void __launch_bounds__(C::NT, C::MINB)
+    fft_stockham_c32_ring_kernel(const __half2* in, const int8_t* in_exp, __half2* out, int8_t* out_exp,
+                                 int64_t batch, const float2* __restrict__ tw, float scale, int* err,
+                                 uint64_t wait_ns, int stall) {
+    constexpr int D = C::PIPE;
+    constexpr int TILE = C::S * C::N;
+    using SM = C32Smem<C>;
+    extern __shared__ __align__(16) float2 smem[];
+    unsigned char* base8 = reinterpret_cast<unsigned char*>(smem);
+    __half2* ring = reinterpret_cast<__half2*>(base8 + SM::kRingOffset);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(base8 + SM::kBarOffset);
+    float* red = reinterpret_cast<float*>(base8 + SM::kRedOffset);
+    const int tid = threadIdx.x;
+    const int sl = tid / C::T;
+    const int t = tid % C::T;
+    const int sb = sl * C::N;
+    const int ls = log2_pow2(scale);
+    const int64_t ntiles = (batch + C::S - 1) / C::S;
+
+    auto issue = [&](int slot, int64_t tile) {  // thread 0 only
+        const int64_t first = tile * C::S;
+        const int64_t left = batch - first;
+        const uint32_t bytes = (uint32_t)((left < C::S ? left : C::S) * C::N * 4);
+        mbar_arrive_expect_tx(&bars[slot], bytes);
+        bulk_copy_g2s(ring + slot * TILE, in + first * C::N, bytes, &bars[slot]);
+    };
+    if (tid == 0) {
+        for (int d = 0; d < D; ++d) mbar_init(&bars[d], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (tid == 0 && !stall) {
+        for (int d = 0; d < D; ++d) {
+            const int64_t tile = blockIdx.x + (int64_t)d * gridDim.x;
+            if (tile < ntiles) issue(d, tile);
+        }
+    }
+    TcCtx tc;  // FP32 butterflies only
+    bool dead = false;
+    if (stall) {  // failure-detection test mode, as in fft_stockham_ring_kernel
+        if (!mbar_wait_bounded(&bars[0], 0, wait_ns)) atomicCAS(err, 0, kErrTimeout);
+        dead = true;
+    }
+    int buf = 0;
+    int64_t it = 0;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+        const int slot = (int)(it % D);
+        const uint32_t parity = (uint32_t)((it / D) & 1);
+        const int64_t sig = tile * C::S + sl;
+        const bool in_range = sig < batch;
+        const int ein = in_range ? (int)in_exp[sig] : 0;
+        if (!dead && !mbar_wait_bounded(&bars[slot], parity, wait_ns)) {
+            dead = true;
+            atomicCAS(err, 0, kErrTimeout);
+        }
+        float2 v[C::E];
+        gather_tile_c32<C, INV>(v, ring + slot * TILE, sb, t);
+        twist_and_dft<C, 0>(v, t, tw, tc);
+        float2* b = smem + buf * TILE;
+        if constexpr (C::kBuffers == 1) __syncthreads();  // previous readers of b are done
+        scatter<C, 0>(v, b, sb, t);
+        __syncthreads();  // every thread is done with ring[slot]
+        if (tid == 0 && !dead && !stall) {
+            const int64_t next = tile + (int64_t)D * gridDim.x;
+            if (next < ntiles) {
+                fence_proxy_async_smem();
+                issue(slot, next);
+            }
+        }
+        gather<C, 1>(v, b, sb, t);
+        if constexpr (C::kBuffers == 2) buf ^= 1;
+        twist_and_dft<C, 1>(v, t, tw, tc);
+        rest_stages<C, 2>(v, smem, buf, sb, t, tw, tc);
+        const C32Out o = c32_out_scale(c32_signal_max<C>(v, red), ein, ls);
+        store_last_c32<C, INV>(v, out + sig * C::N, out_exp + sig, t, in_range && !dead, o);
+    }
+}
+
+// complex32, N = 2..32: one thread owns a whole signal, as in
+// fft_small_kernel.  A warp tile of 32*U signals moves between HBM and the
+// warp's shared-memory slab in 128-bit pieces (4 elements each); each lane
+// finds its own signal's exponent without any exchange.
+template <class SC, bool INV>
+__global__ void __launch_bounds__(SC::NT)
+    fft_small_c32_kernel(const __half2* in, const int8_t* in_exp, __half2* out, int8_t* out_exp, int64_t batch,
+                         const float2* __restrict__ tw, float scale, int* err, uint64_t wait_ns, int stall) {
+    constexpr int N = SC::N, W = SC::WARPS_PER_BLOCK, U = SC::UNROLL;
+    constexpr int TS = 32 * U;         // signals per warp tile
+    constexpr int P = TS * N / 4;      // 128-bit pieces per warp tile
+    extern __shared__ __align__(16) float4 smem4[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float4* sm = smem4 + warp * P;
+    const int ls = log2_pow2(scale);
+    const int64_t wtiles = (batch + TS - 1) / TS;
+    for (int64_t wt = (int64_t)blockIdx.x * W + warp; wt < wtiles; wt += (int64_t)gridDim.x * W) {
+        const int64_t first = wt * TS;
+        const int64_t left = batch - first;
+        const int nsig = (int)(left < TS ? left : TS);
+        const int valid_e = nsig * N;          // binary16 pairs in this tile
+        const int full = valid_e / 4;          // whole 128-bit pieces
+        const float4* src = reinterpret_cast<const float4*>(in + first * N);
+        float4* dst = reinterpret_cast<float4*>(out + first * N);
+#pragma unroll
+        for (int i = 0; i < (P + 31) / 32; ++i) {
+            const int p = lane + 32 * i;
+            if (p < full) sm[swz16(p)] = ld_stream4v<SC::CH>(src + p);
+        }
+        if (N == 2 && lane == 0 && (valid_e & 3))  // odd signal count: the last signal is half a piece
+            reinterpret_cast<float2*>(sm + swz16(full))[0] =
+                *reinterpret_cast<const float2*>(in + first * N + 4 * full);
+        __syncwarp();
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int sg = u * 32 + lane;
+            const bool act = sg < nsig;
+            const int ein = act ? (int)in_exp[first + sg] : 0;
+            float2 v[N];
+            if constexpr (N >= 4) {
+#pragma unroll
+                for (int i = 0; i < N / 4; ++i) {
+                    const float4 f = sm[swz16(sg * (N / 4) + i)];
+                    v[4 * i + 0] = __half22float2(bits_h2(f.x));
+                    v[4 * i + 1] = __half22float2(bits_h2(f.y));
+                    v[4 * i + 2] = __half22float2(bits_h2(f.z));
+                    v[4 * i + 3] = __half22float2(bits_h2(f.w));
+                }
+            } else {
+                const float2 f = reinterpret_cast<const float2*>(sm + swz16(sg >> 1))[sg & 1];
+                v[0] = __half22float2(bits_h2(f.x));
+                v[1] = __half22float2(bits_h2(f.y));
+            }
+            if constexpr (INV) {
+#pragma unroll
+                for (int i = 0; i < N; ++i) v[i].y = -v[i].y;
+            }
+            Dft<N>::run(v);
+            float m = 0.0f;
+#pragma unroll
+            for (int i = 0; i < N; ++i) m = fmaxf(m, fmaxf(fabsf(v[i].x), fabsf(v[i].y)));
+            const C32Out o = c32_out_scale(m, ein, ls);
+            const float my = INV ? -o.mult : o.mult;
+            float hw[N];  // binary16 pairs as 32-bit words
+#pragma unroll
+            for (int i = 0; i < N; ++i) hw[i] = h2_bits(__floats2half2_rn(v[i].x * o.mult, v[i].y * my));
+            if constexpr (N >= 4) {
+#pragma unroll
+                for (int i = 0; i < N / 4; ++i)
+                    sm[swz16(sg * (N / 4) + i)] = make_float4(hw[4 * i], hw[4 * i + 1], hw[4 * i + 2], hw[4 * i + 3]);
+            } else {
+                reinterpret_cast<float2*>(sm + swz16(sg >> 1))[sg & 1] = make_float2(hw[0], hw[1]);
+            }
+            if (act) out_exp[first + sg] = (int8_t)o.e;
+        }
+        __syncwarp();
+#pragma unroll
+        for (int i = 0; i < (P + 31) / 32; ++i) {
+            const int p = lane + 32 * i;
+            if (p < full) st_stream4v<SC::CH>(dst + p, sm[swz16(p)]);
+        }
+        if (N == 2 && lane == 0 && (valid_e & 3))
+            *reinterpret_cast<float2*>(out + first * N + 4 * full) = reinterpret_cast<const float2*>(sm + swz16(full))[0];
+        __syncwarp();
+    }
+}
+
+template <int LOG2N, int WARPS, int U = 1, int CH_ = 0>
+struct SmallC32Cfg : SmallCfg<LOG2N, WARPS, U, CH_> {
+    static constexpr int kSmemBytes = WARPS * 32 * U * (1 << LOG2N) * 4;
+};
 
 }  // namespace gbfft

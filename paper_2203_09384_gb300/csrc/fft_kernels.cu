@@ -58,6 +58,42 @@ static KernelEntry generic_entry(int variant) {
     return e;
 }
 
+template <class C>
+static KernelEntry c32_entry(int variant) {
+    KernelEntry e = generic_entry<C>(variant);
+    e.kind = KernelKind::C32;
+    e.smem_bytes = C32Smem<C>::kBytes;
+    if constexpr (C::PIPE > 0) {
+        e.kernel_fwd = reinterpret_cast<const void*>(&fft_stockham_c32_ring_kernel<C, false>);
+        e.kernel_inv = reinterpret_cast<const void*>(&fft_stockham_c32_ring_kernel<C, true>);
+    } else {
+        e.kernel_fwd = reinterpret_cast<const void*>(&fft_stockham_c32_kernel<C, false>);
+        e.kernel_inv = reinterpret_cast<const void*>(&fft_stockham_c32_kernel<C, true>);
+    }
+    return e;
+}
+
+template <class SC>
+static KernelEntry small_c32_entry(int variant) {
+    KernelEntry e{};
+    e.log2n = 0;
+    while ((1 << e.log2n) < SC::N) ++e.log2n;
+    e.variant = variant;
+    e.kind = KernelKind::C32;
+    e.elems_per_thread = SC::N;
+    e.signals_per_block = 32 * SC::UNROLL * SC::WARPS_PER_BLOCK;
+    e.threads_per_block = SC::NT;
+    e.smem_bytes = SC::kSmemBytes;
+    e.num_stages = 1;
+    e.radix[0] = SC::N;
+    e.min_blocks = 1;
+    e.twiddles = 0;
+    e.kernel_fwd = reinterpret_cast<const void*>(&fft_small_c32_kernel<SC, false>);
+    e.kernel_inv = reinterpret_cast<const void*>(&fft_small_c32_kernel<SC, true>);
+    e.fill_twiddles = &fill_nothing;
+    return e;
+}
+
 template <class SC>
 static KernelEntry small_entry(int variant) {
     KernelEntry e{};
@@ -161,5 +197,12 @@ int GBFFT_ENTRIES_FN(GBFFT_LOG2N)(gbfft::KernelEntry* out, int max) {
 #define GBFFT_SX(L, V, W, U, CH) GBFFT_ONLY_##L(put(small_entry<SmallCfg<L, W, U, CH>>(V));)
     GBFFT_SMALL_SCHEDULES(GBFFT_SX)
 #undef GBFFT_SX
+#define GBFFT_CX(L, V, E, S, R0, R1, R2, R3, MINB, PIPE, XB) \
+    GBFFT_ONLY_##L(put(c32_entry<Cfg<L, E, S, R0, R1, R2, R3, MINB, PIPE, 0, XB, 0>>(V));)
+    GBFFT_C32_SCHEDULES(GBFFT_CX)
+#undef GBFFT_CX
+#define GBFFT_SCX(L, V, W, U, CH) GBFFT_ONLY_##L(put(small_c32_entry<SmallC32Cfg<L, W, U, CH>>(V));)
+    GBFFT_C32_SMALL_SCHEDULES(GBFFT_SCX)
+#undef GBFFT_SCX
     return count;
 }

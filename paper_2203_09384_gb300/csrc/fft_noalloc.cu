@@ -154,7 +154,7 @@ extern "C" fft_status_t fft_execute_noalloc(int64_t n, int64_t batch, int direct
     const int log2n = ilog2_exact(n);
     const int variant = (int)((flags & FFT_FLAG_VARIANT_MASK) >> 8) - 1;
     const gbfft::KernelEntry* e = gbfft::lookup_entry(log2n, variant);
-    if (!e || e->tc != 0) return FFT_ERR_INVALID_VALUE;  // FP32 schedules only
+    if (!e || e->tc != 0 || e->kind == gbfft::KernelKind::C32) return FFT_ERR_INVALID_VALUE;  // FP32, complex64 only
     if (e->twiddles > kNoAllocTwiddles) return FFT_ERR_NOALLOC_LIMIT;
 
     int dev = -1;

@@ -278,8 +278,10 @@ fft_status_t fft_validate(int64_t n, int64_t batch, int direction, int dtype, ui
     if (batch < 0) return FFT_ERR_INVALID_VALUE;
     if (batch > INT64_MAX / (16 * n)) return FFT_ERR_INVALID_VALUE;  // byte count must fit
     if (direction != FFT_FORWARD && direction != FFT_INVERSE) return FFT_ERR_INVALID_VALUE;
-    if (dtype != FFT_C64 && dtype != FFT_C64_TC_F16 && dtype != FFT_C64_TC_BF16) return FFT_ERR_INVALID_VALUE;
+    if (dtype != FFT_C64 && dtype != FFT_C64_TC_F16 && dtype != FFT_C64_TC_BF16 && dtype != FFT_C32)
+        return FFT_ERR_INVALID_VALUE;
     if (flags & ~kKnownFlags) return FFT_ERR_INVALID_VALUE;
+    if (dtype == FFT_C32 && (flags & FFT_FLAG_HOST_STAGING)) return FFT_ERR_UNSUPPORTED;
     return FFT_OK;
 }
 
@@ -306,21 +308,24 @@ fft_status_t fft_plan_create_ex(int64_t n, int64_t batch, int direction, int dty
     const int log2n = ilog2(n);
     LengthVariants* lv = &registry()[log2n];
     const int want_tc = dtype == FFT_C64_TC_F16 ? 1 : dtype == FFT_C64_TC_BF16 ? 2 : 0;
+    const bool want_c32 = dtype == FFT_C32;
     int variant = (int)((flags & FFT_FLAG_VARIANT_MASK) >> 8) - 1;
     if (variant < 0) {
         // FP32: the length's default.  Tensor-core types: the first variant of
         // that type; lengths without a radix-16 tensor-core schedule run FP32.
+        // complex32 storage: the first complex32 variant.
         variant = lv->preferred.load();
-        if (want_tc) {
-            for (int v = 0; v < lv->count; ++v)
-                if (lv->v[v].kernel_fwd && lv->v[v].tc == want_tc) {
-                    variant = v;
-                    break;
-                }
+        for (int v = 0; v < lv->count && (want_tc || want_c32); ++v) {
+            const KernelEntry& c = lv->v[v];
+            if (c.kernel_fwd && ((want_c32 && c.kind == KernelKind::C32) || (want_tc && c.tc == want_tc))) {
+                variant = v;
+                break;
+            }
         }
     }
     if (variant >= lv->count || !lv->v[variant].kernel_fwd) return FFT_ERR_INVALID_VALUE;
     if (lv->v[variant].tc != 0 && lv->v[variant].tc != want_tc) return FFT_ERR_INVALID_VALUE;
+    if ((lv->v[variant].kind == KernelKind::C32) != want_c32) return FFT_ERR_INVALID_VALUE;
     const KernelEntry* e = &lv->v[variant];
     gbfft_plan* p = new (std::nothrow) gbfft_plan();
     if (!p) return FFT_ERR_ALLOC;
@@ -422,7 +427,8 @@ fft_status_t fft_plan_create_ragged(const int64_t* offsets_host, int64_t count, 
                                     uint32_t flags, fft_plan_t* plan) {
     if (!plan) return FFT_ERR_INVALID_VALUE;
     if (direction != FFT_FORWARD && direction != FFT_INVERSE) return FFT_ERR_INVALID_VALUE;
-    if (dtype != FFT_C64 && dtype != FFT_C64_TC_F16 && dtype != FFT_C64_TC_BF16) return FFT_ERR_INVALID_VALUE;
+    if (dtype != FFT_C64 && dtype != FFT_C64_TC_F16 && dtype != FFT_C64_TC_BF16 && dtype != FFT_C32)
+        return FFT_ERR_INVALID_VALUE;
     if (flags & ~kKnownFlags) return FFT_ERR_INVALID_VALUE;
     if (dtype != FFT_C64) return FFT_ERR_UNSUPPORTED;
     if (count < 0 || (count > 0 && !offsets_host)) return FFT_ERR_INVALID_VALUE;
@@ -459,8 +465,40 @@ fft_status_t fft_plan_create(int64_t n, int64_t batch, int direction, int dtype,
     return fft_plan_create_ex(n, batch, direction, dtype, 0u, plan);
 }
 
+fft_status_t fft_execute_c32(fft_plan_t p, const void* in, const int8_t* in_exp, void* out, int8_t* out_exp,
+                             void* stream) {
+    if (!p || p->ragged || !p->entry || p->entry->kind != KernelKind::C32) return FFT_ERR_INVALID_VALUE;
+    if (p->batch == 0) return FFT_OK;
+    if (!in || !out || !in_exp || !out_exp) return FFT_ERR_INVALID_VALUE;
+    if (((uintptr_t)in & 15) || ((uintptr_t)out & 15)) return FFT_ERR_MISALIGNED;
+    const uintptr_t bytes = (uintptr_t)(p->n * p->batch * 4);
+    const uintptr_t a = (uintptr_t)in, b = (uintptr_t)out;
+    if (a != b && a < b + bytes && b < a + bytes) return FFT_ERR_OVERLAP;
+    const uintptr_t ea = (uintptr_t)in_exp, eb = (uintptr_t)out_exp, eb_n = (uintptr_t)p->batch;
+    if (ea != eb && ea < eb + eb_n && eb < ea + eb_n) return FFT_ERR_OVERLAP;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != p->device) return FFT_ERR_INVALID_VALUE;
+    const KernelEntry* e = p->entry;
+    int64_t batch = p->batch;
+    const void* in2 = in;
+    void* out2 = out;
+    const float2* tw = (const float2*)p->d_twiddles;
+    float scale = p->scale;
+    int* err = p->d_error;
+    uint64_t wait_ns = p->wait_ns;
+    int stall = (p->flags & FFT_FLAG_TEST_STALL) ? 1 : 0;
+    void* args[] = {&in2, &in_exp, &out2, &out_exp, &batch, &tw, &scale, &err, &wait_ns, &stall};
+    if (cudaLaunchKernel(p->kernel, dim3((unsigned)p->grid), dim3(e->threads_per_block), args,
+                         (size_t)e->smem_bytes, (cudaStream_t)stream) != cudaSuccess) {
+        cudaGetLastError();
+        return FFT_ERR_CUDA;
+    }
+    return FFT_OK;
+}
+
 fft_status_t fft_execute(fft_plan_t p, const void* in, void* out, void* stream) {
     if (!p) return FFT_ERR_INVALID_VALUE;
+    if (p->entry && p->entry->kind == KernelKind::C32) return FFT_ERR_INVALID_VALUE;  // fft_execute_c32
     if (p->ragged) {
         int dev = -1;
         if (cudaGetDevice(&dev) != cudaSuccess || dev != p->device) return FFT_ERR_INVALID_VALUE;
@@ -479,7 +517,7 @@ fft_status_t fft_execute(fft_plan_t p, const void* in, void* out, void* stream) 
 }
 
 fft_status_t fft_execute_host(fft_plan_t p, const void* in_host, void* out_host, void* stream) {
-    if (!p || p->ragged) return FFT_ERR_INVALID_VALUE;
+    if (!p || p->ragged || p->entry->kind == KernelKind::C32) return FFT_ERR_INVALID_VALUE;
     if (p->batch == 0) return FFT_OK;
     if (!p->stages) return FFT_ERR_INVALID_VALUE;  // plan made without FFT_FLAG_HOST_STAGING
     if (!in_host || !out_host) return FFT_ERR_INVALID_VALUE;
@@ -588,7 +626,8 @@ int fft_variant_count(int64_t n) {
 fft_status_t fft_set_default_variant(int64_t n, int variant) {
     if (n < 2 || n > 2048 || (n & (n - 1)) != 0) return FFT_ERR_INVALID_SIZE;
     LengthVariants* lv = &registry()[ilog2(n)];
-    if (variant < 0 || variant >= lv->count || !lv->v[variant].kernel_fwd || lv->v[variant].tc != 0)
+    if (variant < 0 || variant >= lv->count || !lv->v[variant].kernel_fwd || lv->v[variant].tc != 0 ||
+        lv->v[variant].kind == KernelKind::C32)
         return FFT_ERR_INVALID_VALUE;
     lv->preferred.store(variant);
     return FFT_OK;
@@ -598,6 +637,7 @@ int fft_variant_dtype(int64_t n, int variant) {
     if (n < 2 || n > 2048 || (n & (n - 1)) != 0) return -1;
     LengthVariants* lv = &registry()[ilog2(n)];
     if (variant < 0 || variant >= lv->count || !lv->v[variant].kernel_fwd) return -1;
+    if (lv->v[variant].kind == KernelKind::C32) return FFT_C32;
     const int tc = lv->v[variant].tc;
     return tc == 1 ? FFT_C64_TC_F16 : tc == 2 ? FFT_C64_TC_BF16 : FFT_C64;
 }

@@ -11,7 +11,7 @@
 
 namespace gbfft {
 
-enum class KernelKind : int { Small = 0, Direct = 1, Ring = 2 };
+enum class KernelKind : int { Small = 0, Direct = 1, Ring = 2, C32 = 4 };
 
 struct KernelEntry {
     int log2n;

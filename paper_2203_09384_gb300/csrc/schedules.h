@@ -76,6 +76,36 @@
     SX(5, 0, 2, 2, 0)                \
     SX(5, 2, 4, 1, 0)
 
+// complex32-storage rows (FFT_C32): CX(log2N, variant, E, S, R0..R3, MINB,
+// PIPE, XB) as in GX, the Stockham kernel with binary16 loads/stores and
+// per-signal exponents, FP32 arithmetic; PIPE >= 2 stages the binary16 tiles
+// through a bulk-copy ring.  A length's first complex32 row is its default;
+// for N <= 32 that is the one-thread-per-signal SCX row further down.
+#define GBFFT_C32_SCHEDULES(CX)                   \
+    CX(1, 3, 2, 256, 2, 0, 0, 0, 1, 0, 0)        \
+    CX(2, 5, 2, 128, 2, 2, 0, 0, 1, 0, 0)        \
+    CX(3, 4, 4, 128, 2, 4, 0, 0, 1, 0, 0)        \
+    CX(4, 4, 8, 128, 4, 4, 0, 0, 1, 0, 0)        \
+    CX(5, 4, 16, 128, 8, 4, 0, 0, 1, 0, 0)       \
+    CX(6, 1, 16, 64, 8, 8, 0, 0, 1, 0, 0)        \
+    CX(7, 5, 16, 32, 8, 16, 0, 0, 1, 0, 0)       \
+    CX(8, 5, 16, 16, 16, 16, 0, 0, 3, 2, 1)      \
+    CX(8, 6, 16, 16, 16, 16, 0, 0, 1, 0, 0)      \
+    CX(9, 2, 16, 8, 8, 8, 8, 0, 2, 0, 0)         \
+    CX(10, 8, 16, 2, 8, 16, 8, 0, 2, 3, 0)       \
+    CX(10, 9, 16, 2, 8, 16, 8, 0, 2, 0, 0)       \
+    CX(11, 8, 16, 1, 8, 16, 16, 0, 3, 3, 0)      \
+    CX(11, 9, 16, 1, 8, 16, 16, 0, 3, 0, 0)
+
+// complex32 one-thread-per-signal rows (N <= 32): SCX(log2N, variant, warps
+// per block, 32-signal groups per warp tile, cache hints)
+#define GBFFT_C32_SMALL_SCHEDULES(SCX) \
+    SCX(1, 2, 8, 4, 0)                  \
+    SCX(2, 4, 4, 8, 0)                  \
+    SCX(3, 3, 8, 4, 0)                  \
+    SCX(4, 3, 4, 4, 0)                  \
+    SCX(5, 3, 4, 2, 0)
+
 #define GBFFT_MIN_LOG2N 1
 #define GBFFT_MAX_LOG2N 11
-#define GBFFT_MAX_VARIANTS 8
+#define GBFFT_MAX_VARIANTS 10

@@ -23,3 +23,35 @@ def max_rel_l2(got, ref) -> float:
 
 def to_np(t: torch.Tensor) -> np.ndarray:
     return t.detach().cpu().numpy().astype(np.complex128)
+
+
+def c32_encode(x) -> tuple[torch.Tensor, torch.Tensor]:
+    """complex32 storage of complex values [batch, n]: binary16 (re, im) pairs
+    and one int8 exponent per signal, value = stored * 2^exp, the exponent
+    putting the signal's largest component in [2^14, 2^15).  Returns CPU
+    tensors (torch.complex32 [batch, n], torch.int8 [batch])."""
+    z = np.asarray(x, dtype=np.complex128)
+    m = np.maximum(np.abs(z.real), np.abs(z.imag)).max(axis=1)
+    e = np.where(m > 0, np.frexp(m)[1] - 15, 0).astype(np.int64)
+    pairs = np.stack([z.real, z.imag], axis=-1) * np.ldexp(1.0, -e)[:, None, None]
+    h = torch.from_numpy(pairs.astype(np.float16).reshape(z.shape[0], -1).copy())
+    return h.view(torch.complex32), torch.from_numpy(e.astype(np.int8))
+
+
+def c32_decode(stored: torch.Tensor, exp: torch.Tensor) -> np.ndarray:
+    """Inverse of c32_encode (exact): complex128 [batch, n]."""
+    h = stored.detach().contiguous().view(torch.float16).cpu().numpy().astype(np.float64)
+    h = h.reshape(stored.shape[0], -1, 2)
+    e = exp.detach().cpu().numpy().astype(np.int64)
+    return (h[..., 0] + 1j * h[..., 1]) * np.ldexp(1.0, e)[:, None]
+
+
+def c32_max_stored(stored: torch.Tensor) -> np.ndarray:
+    """Largest |component| of each signal as stored (before the exponent)."""
+    h = stored.detach().contiguous().view(torch.float16).cpu().numpy().astype(np.float64)
+    return np.abs(h.reshape(stored.shape[0], -1)).max(axis=1)
+
+
+def c32_to(x: torch.Tensor, device) -> torch.Tensor:
+    """Move a complex32 tensor (through its binary16 view)."""
+    return x.contiguous().view(torch.float16).to(device).view(torch.complex32)

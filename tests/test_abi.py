@@ -56,6 +56,20 @@ def test_valid_arguments():
     for k in range(1, 12):
         assert _abi.fft_validate(2 ** k, 0) == 0
         assert _abi.fft_validate(2 ** k, 3, 1, 0, _abi.FFT_FLAG_UNNORMALIZED) == 0
+        assert _abi.fft_validate(2 ** k, 3, 0, _abi.FFT_C32) == 0
+
+
+def test_complex32_registry():
+    """Each length has complex32-storage variants; they are refused as the
+    default of the complex64 path and with host staging."""
+    for k in range(1, 12):
+        n = 2 ** k
+        kinds = [_abi.lib().fft_variant_dtype(n, v) for v in range(_abi.fft_variant_count(n))]
+        assert 1 <= kinds.count(_abi.FFT_C32) <= 2
+        assert kinds[_abi.fft_get_default_variant(n)] == _abi.FFT_C64
+    assert _abi.fft_validate(64, 1, 0, _abi.FFT_C32, _abi.FFT_FLAG_HOST_STAGING) == \
+        _abi.STATUS_CODE["FFT_ERR_UNSUPPORTED"]
+    assert _abi.fft_validate(64, 1, dtype=4) == _abi.STATUS_CODE["FFT_ERR_INVALID_VALUE"]
 
 
 def test_null_arguments(L):

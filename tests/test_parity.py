@@ -202,7 +202,7 @@ def test_variant_selection():
             p = gb.Plan(n, 64, variant=v, dtype=dt)
             assert p.info().variant == v
             p.close()
-            if dt != "c64":  # a tensor-core variant is refused for FP32 plans
+            if dt != "c64":  # a tensor-core or complex32 variant is refused for FP32 plans
                 with pytest.raises(gb.FFTError):
                     gb.Plan(n, 64, variant=v)
         with pytest.raises(gb.FFTError):

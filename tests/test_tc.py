@@ -93,7 +93,7 @@ def _tc_variants():
     for n in [2 ** k for k in range(1, 12)]:
         for v in range(gb.fft_variant_count(n)):
             dt = gb.fft_variant_dtype(n, v)
-            if dt != gb.FFT_C64:
+            if dt in (gb.FFT_C64_TC_F16, gb.FFT_C64_TC_BF16):
                 out.append((n, v, gb.DTYPE_NAMES[dt]))
     return out
 
