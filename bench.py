@@ -402,15 +402,31 @@ def run_ours(args):
     if args.only_n:
         LOG2NS = [int(math.log2(int(v))) for v in args.only_n.split(",")]
     x = synth.uniform(1, ELEMS, seed=1 + rank, device=dev).reshape(-1)
-    out = torch.empty_like(x)
     plans = {k: gb.Plan(2 ** k, ELEMS // 2 ** k, device=dev, dtype=args.dtype) for k in LOG2NS}
+    c32 = args.dtype == "c32"
+    if c32:
+        # complex32 storage: the same U[-1, 1] values rounded to binary16, input
+        # exponents 0 (any exponent is valid input); one exponent byte per signal
+        # each way, so a length moves 8 B per element + 2 B per signal
+        xh = torch.view_as_real(x).half().reshape(-1).view(torch.complex32)
+        outh = torch.empty_like(xh)
+        ein = {k: torch.zeros(ELEMS >> k, dtype=torch.int8, device=dev) for k in LOG2NS}
+        eout = {k: torch.empty(ELEMS >> k, dtype=torch.int8, device=dev) for k in LOG2NS}
+        del x
+    else:
+        out = torch.empty_like(x)
+    len_bytes = {k: (8 * ELEMS + 2 * (ELEMS >> k)) if c32 else BYTES_PER_ELEM * ELEMS for k in LOG2NS}
 
     def step(events=None):
         for i, k in enumerate(LOG2NS):
             p = plans[k]
             if events is not None:
                 events[i][0].record(stream)
-            gb.fft_execute(p.handle, x.data_ptr(), out.data_ptr(), stream.cuda_stream)
+            if c32:
+                gb.fft_execute_c32(p.handle, xh.data_ptr(), ein[k].data_ptr(), outh.data_ptr(), eout[k].data_ptr(),
+                                   stream.cuda_stream)
+            else:
+                gb.fft_execute(p.handle, x.data_ptr(), out.data_ptr(), stream.cuda_stream)
             if events is not None:
                 events[i][1].record(stream)
 
@@ -447,7 +463,7 @@ def run_ours(args):
     # end-to-end through the C-ABI with pinned host buffers: fft_execute_host
     # pipelines copy-in / transform / copy-out per chunk over three streams
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and not c32:  # fft_execute_host is complex64 only
         hx = torch.empty(ELEMS, dtype=torch.complex64, pin_memory=True)
         hx.copy_(x)
         hy = torch.empty_like(hx, pin_memory=True)
@@ -482,35 +498,37 @@ def run_ours(args):
             dist.destroy_process_group()
         return 0
 
-    step_bytes = BYTES_PER_ELEM * ELEMS * len(LOG2NS)
+    step_bytes = sum(len_bytes.values())
     ms_per_step = ms / args.steps
     value = whole_job_gbs(step_bytes, world, ms_per_step)
     peak, peak_src = peaks()
     per_n = {}
     for k in LOG2NS:
         avg = statistics.mean(per_launch[k])
-        gbs = BYTES_PER_ELEM * ELEMS / (avg * 1e-3) / 1e9
+        gbs = len_bytes[k] / (avg * 1e-3) / 1e9
         per_n[str(2 ** k)] = {"ms": round(avg, 4), "gbs": round(gbs, 1),
                               "frac": round(gbs / peak, 4),
                               "gflops": round(ELEMS * flops_per_elem(2 ** k) / (avg * 1e-3) / 1e9, 1)}
     dom = max(LOG2NS, key=lambda k: statistics.mean(per_launch[k]))
     dom_ms = statistics.mean(per_launch[dom])
-    achieved = BYTES_PER_ELEM * ELEMS / (dom_ms * 1e-3) / 1e9
-    traffic = ncu_traffic(dom)
+    achieved = len_bytes[dom] / (dom_ms * 1e-3) / 1e9
+    traffic = ncu_traffic(dom) if args.dtype == "c64" else None
     line = {
         "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": {"c64": "f32", "tc_f16": "f16-tensor-core+f32", "tc_bf16": "bf16-tensor-core+f32"}[args.dtype],
+        "dtype": {"c64": "f32", "tc_f16": "f16-tensor-core+f32", "tc_bf16": "bf16-tensor-core+f32",
+                  "c32": "f16-storage+f32"}[args.dtype],
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "lengths": [2 ** k for k in LOG2NS],
                    "elements_per_length": ELEMS, "bytes_per_step_per_gpu": step_bytes,
-                   "l2": "inputs 2 GiB per length, 16x L2: no flush needed",
+                   "l2": ("inputs 1 GiB per length (complex32), 8x L2: no flush needed" if c32
+                          else "inputs 2 GiB per length, 16x L2: no flush needed"),
                    "parallelism": f"replicas x{world}", "per_n": per_n},
         "roofline": {"bound": "hbm", "kernel": f"fft N={2 ** dom}", "achieved": round(achieved, 1),
                      "peak": peak, "peak_source": peak_src, "unit": "GB/s",
                      "frac": round(achieved / peak, 4),
-                     "traffic": traffic, "algorithmic_bytes": BYTES_PER_ELEM * ELEMS},
+                     "traffic": traffic, "algorithmic_bytes": len_bytes[dom]},
         "e2e": e2e,
         "gpu_launches": args.steps * len(LOG2NS),
         "clocks": clocks,
@@ -537,8 +555,8 @@ def main(argv=None):
                     help="skip the adjoint / ragged / tensor-core workloads")
     ap.add_argument("--only-n", default="", help="comma list of lengths (profiling runs)")
     ap.add_argument("--elems", type=int, default=0, help="elements per length (profiling runs)")
-    ap.add_argument("--dtype", default="c64", choices=["c64", "tc_f16", "tc_bf16"],
-                    help="arithmetic of the sweep (profiling runs of the tensor-core path)")
+    ap.add_argument("--dtype", default="c64", choices=["c64", "tc_f16", "tc_bf16", "c32"],
+                    help="arithmetic / storage of the sweep (runs of the tensor-core and complex32 paths)")
     args = ap.parse_args(argv)
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
