@@ -1,6 +1,6 @@
 """The FP64 oracle against its pins, and the pins against planted mistakes.
 
-CPU only (no GPU marker): the driver runs these with ``-m "not gpu"``.
+CPU only (no GPU marker): these run under ``-m "not gpu"``.
 """
 import numpy as np
 import pytest

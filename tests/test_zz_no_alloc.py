@@ -74,7 +74,7 @@ def test_allocates_no_device_memory():
             _abi.fft_execute_noalloc(k, (n * batch) // k, 1, 0, x.data_ptr(), out.data_ptr(), s)
         torch.cuda.synchronize()
 
-    sweep()  # set-up calls; the driver also loads each kernel's code on first launch
+    sweep()  # set-up calls; the CUDA driver also loads each kernel's code on first launch
     free_before, _ = torch.cuda.mem_get_info()
     sweep()
     sweep()
