@@ -176,6 +176,13 @@ def cpu_baseline(budget_s: float = 12.0, threads: int | None = None):
             "per_n_gbs": detail}
 
 
+def tc_stage_count(info) -> int:
+    """Radix-16 stages a plan runs on tensor cores (0 for an FP32 plan)."""
+    if info.tc == 0:
+        return 0
+    return sum(1 for s in range(info.num_stages) if info.radix[s] == 16)
+
+
 def _time_ms(fn, stream, reps: int = 10, warmup: int = 3) -> float:
     import torch
     for _ in range(warmup):
@@ -295,7 +302,7 @@ def run_extras(dev, stream, peak):
             d = torch.linalg.vector_norm(o - ref, dim=1) / torch.linalg.vector_norm(ref, dim=1)
             res[dt] = {"gbs": gbs(n * b, ms), "frac": round(gbs(n * b, ms) / peak, 4), "ms": round(ms, 4),
                        "gelem_s": round(n * b / ms / 1e6, 2),
-                       "max_rel_l2_vs_fp32_path": float(d.max()), "tc_stages": int(p.info().tc != 0)}
+                       "max_rel_l2_vs_fp32_path": float(d.max()), "tc_stages": tc_stage_count(p.info())}
         # complex32 storage: 4 B per element each way plus one exponent byte per signal
         hs, he = encode_c32(xs)
         p = gb.Plan(n, b, dtype="c32", device=dev)

@@ -291,15 +291,29 @@ __device__ __forceinline__ uint64_t global_timer_ns() {
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
 }
+// try_wait with a suspend-time hint: the thread sleeps until the phase
+// completes or about hint_ns pass, instead of polling (a polling warp takes
+// issue slots from the warps that have work)
+__device__ __forceinline__ bool mbar_try_wait_suspend(uint64_t* bar, uint32_t parity, uint32_t hint_ns) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(hint_ns)
+        : "memory");
+    return ok != 0;
+}
+constexpr uint32_t kSuspendHintNs = 100000;  // 100 us: also the timeout check granularity
+
 // Wait for phase `parity` of `bar` to complete, giving up after limit_ns of
 // wall time.  Returns false on timeout (the caller records the error).
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint64_t limit_ns) {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = global_timer_ns();
     for (;;) {
-#pragma unroll 1
-        for (int i = 0; i < 32; ++i)
-            if (mbar_try_wait(bar, parity)) return true;
+        if (mbar_try_wait_suspend(bar, parity, kSuspendHintNs)) return true;
         if (global_timer_ns() - t0 > limit_ns) return false;
     }
 }
@@ -326,18 +340,29 @@ struct Cfg {
     // a signal never spans warps, so exchanges need only warp syncs (the
     // bulk-copy ring refills after a block-wide barrier, so it uses those)
     static constexpr bool kWarpLocal = T <= 32 && PIPE_ == 0;
+    // XB = -1 / -2 (bulk-copy ring only): no exchange buffer of its own; every
+    // exchange reuses the ring slot the tile arrived in, which is refilled
+    // once the next tile's first barrier shows the block is done with it.
+    // With -2 the tensor-core A operand lives in that slot too (one more
+    // barrier per tensor-core stage, 8 KiB less per block).  Less shared
+    // memory, more resident blocks.
+    static constexpr bool kInRing = XB_ < 0;
+    static constexpr bool kAInRing = XB_ == -2;
     // exchange buffers: one suffices when a signal stays in one warp; across
     // warps two let one barrier per exchange do (XB = 1 forces one buffer and
     // a second barrier, halving the shared memory of the exchange)
-    static constexpr int kBuffers = XB_ ? XB_ : (kWarpLocal ? 1 : 2);
-    static constexpr int kSmemElems = kBuffers * S * N;           // exchange buffers
+    static constexpr int kBuffers = kInRing ? 1 : XB_ ? XB_ : (kWarpLocal ? 1 : 2);
+    static constexpr int kSmemElems = kInRing ? 0 : kBuffers * S * N;  // exchange buffers
     static constexpr int kRingElems = PIPE * S * N;               // prefetch ring
     // 0: FP32 butterflies; 1 / 2: radix-16 stages on FP16 / BF16 tensor cores
     static constexpr int TC = TC_;
     static constexpr int kTcTiles = NT / 128;  // 128-row MMA tiles per radix-16 stage
     static constexpr int kTcCols = 32 * kTcTiles;  // TMEM columns (FP32 accumulators)
     static constexpr int kTcOffset = (((kSmemElems + kRingElems) * 8 + 8 * PIPE) + 127) / 128 * 128;
-    static constexpr int kTcBytes = TC ? kTcTiles * 8192 + 2048 + 128 : 0;
+    // A operand (kTcTiles x 8 KiB, unless it lives in the ring slot), B (2 KiB),
+    // the MMA-completion mbarrier and the TMEM address slot
+    static constexpr int kTcABytes = kAInRing ? 0 : kTcTiles * 8192;
+    static constexpr int kTcBytes = TC ? kTcABytes + 2048 + 128 : 0;
     static constexpr int kSmemBytes = TC ? kTcOffset + kTcBytes : (kSmemElems + kRingElems) * 8 + 8 * PIPE;
     __host__ __device__ static constexpr int radix(int s) {
         return s == 0 ? R0 : s == 1 ? R1 : s == 2 ? R2 : R3;
@@ -362,6 +387,8 @@ struct Cfg {
                   "every radix must divide E");
     static_assert(32 % T == 0 || T % 32 == 0, "T must tile warps");
     static_assert(PIPE == 0 || PIPE >= 2, "the bulk-copy ring needs at least two slots");
+    static_assert(!kInRing || PIPE >= 2, "exchanges in the ring slot need the bulk-copy ring");
+    static_assert(!kAInRing || TC == 0 || kTcTiles * 8192 <= S * N * 8, "the A operand must fit in a ring slot");
     static_assert(TC == 0 || (E == 16 && NT % 128 == 0 && (kTcCols == 32 || kTcCols == 64 || kTcCols == 128)),
                   "tensor-core radix-16 stages need one 16-point butterfly per thread and 128-row tiles");
 };
@@ -379,6 +406,11 @@ struct Cfg {
 // own butterfly's 16 outputs again.  Operands are in the canonical K-major
 // layout without swizzle: 8-row x 16-byte core matrices, 128 B apart along K
 // (leading byte offset) and 512 B apart along M/N (stride byte offset).
+//
+// Dynamic range: each butterfly row is scaled by its own power of two before
+// the FP16 / BF16 conversion (see tc_dft16), which gives every row at least
+// the precision a per-signal power-of-two scale gives the signal's largest
+// row, with no exchange between threads.
 // ---------------------------------------------------------------------------
 struct TcCtx {
     uint32_t tmem = 0;   // TMEM base address of the accumulators
@@ -445,8 +477,8 @@ __device__ __forceinline__ float2 cs16(int m) {
 
 template <class C>
 __device__ __forceinline__ void tc_setup(TcCtx& tc, unsigned char* base, int* err, uint64_t wait_ns) {
-    tc.a = base;
-    tc.b = base + C::kTcTiles * 8192;
+    tc.a = base;  // XB = -2 schedules point this at the tile's slot before each use
+    tc.b = base + C::kTcABytes;
     tc.bar = reinterpret_cast<uint64_t*>(tc.b + 2048);
     uint32_t* slot = reinterpret_cast<uint32_t*>(tc.b + 2048 + 8);
     tc.err = err;
@@ -490,6 +522,18 @@ __device__ __forceinline__ void tc_teardown(TcCtx& tc) {
     }
 }
 
+// 2^k as a float, k in [-126, 127]
+__device__ __forceinline__ float exp2i(int k) { return __uint_as_float((uint32_t)(127 + k) << 23); }
+
+// e with mx = m 2^e, m in [1/2, 1), read off the biased exponent field
+// (mx >= 0); clamped to [-120, 126] so that 2^-e and 2^e are normal floats
+// (zero and subnormal maxima take -120: any power-of-two scale is exact for
+// them).
+__device__ __forceinline__ int pow2_exponent(float mx) {
+    const int e = (int)(__float_as_uint(mx) >> 23) - 126;
+    return e < -120 ? -120 : (e > 126 ? 126 : e);
+}
+
 // Every thread of the block calls this with its own butterfly's 16 inputs.
 // The 16-point DFT is linear, so each row is scaled by its own power of two
 // 2^-e (exact) before the FP16/BF16 conversion, which keeps every operand in
@@ -502,12 +546,13 @@ __device__ __forceinline__ void tc_dft16(float2* v, TcCtx& tc) {
     float mx = 0.0f;
 #pragma unroll
     for (int i = 0; i < 16; ++i) mx = fmaxf(mx, fmaxf(fabsf(v[i].x), fabsf(v[i].y)));
-    int e = 0;
-    frexpf(mx, &e);
-    e = mx > 0.0f ? (e < -120 ? -120 : e) : 0;
-    const float down = ldexpf(1.0f, -e), up = ldexpf(1.0f, e);
+    const int e = pow2_exponent(mx);
+    const float down = exp2i(-e), up = exp2i(e);
 #pragma unroll
     for (int i = 0; i < 16; ++i) v[i] = make_float2(v[i].x * down, v[i].y * down);
+    // XB = -2 writes A over the slot the inputs were just gathered from:
+    // every thread must be done reading it
+    if constexpr (C::kAInRing) __syncthreads();
     unsigned char* arow = tc.a + (tid >> 7) * 8192 + (row >> 3) * 512 + (row & 7) * 16;
 #pragma unroll
     for (int c = 0; c < 4; ++c) {  // K chunk c: Re x_0..7, Re x_8..15, Im x_0..7, Im x_8..15
@@ -675,8 +720,13 @@ __device__ __forceinline__ void store_last(float2 (&v)[C::E], float2* dst, int t
     constexpr int K = C::E / R;
     constexpr int stride = C::N / R;
     if (!active) return;
+    if (scale != 1.0f) {
 #pragma unroll
-    for (int i = 0; i < C::E; ++i) v[i] = make_float2(v[i].x * scale, (INV ? -v[i].y : v[i].y) * scale);
+        for (int i = 0; i < C::E; ++i) v[i] = make_float2(v[i].x * scale, (INV ? -v[i].y : v[i].y) * scale);
+    } else if constexpr (INV) {
+#pragma unroll
+        for (int i = 0; i < C::E; ++i) v[i].y = -v[i].y;
+    }
     if constexpr (K >= 2) {
 #pragma unroll
         for (int q = 0; q < R; ++q) {
@@ -842,6 +892,111 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
         if constexpr (C::kBuffers == 2) buf ^= 1;
         twist_and_dft<C, 1>(v, t, tw, tc);
         rest_stages<C, 2>(v, smem, buf, sb, t, tw, tc);
+        const bool active = sig < batch && !dead && !tc.dead;
+        store_last<C, INV>(v, out + sig * C::N, t, active, scale);
+    }
+    if constexpr (C::TC != 0) tc_teardown<C>(tc);
+}
+
+// Stages 1..M-1 of an in-ring schedule: every exchange goes through the one
+// ring slot `b` that holds the tile.  Before a scatter, the block must be done
+// reading `b`: after an FP32 stage that takes a barrier; after a tensor-core
+// stage it is already so (every thread passed the barrier before the MMA
+// after its gather, and the MMA's reads of A ended before its completion
+// wait returned).
+template <class C, int s>
+__device__ __forceinline__ void rest_stages_in_ring(float2 (&v)[C::E], float2* b, int sb, int t,
+                                                    const float2* __restrict__ tw, TcCtx& tc) {
+    if constexpr (s < C::M) {
+        constexpr bool prev_tc = C::TC != 0 && C::radix(s - 1) == 16 && C::E == 16;
+        if constexpr (!prev_tc) __syncthreads();
+        scatter<C, s - 1>(v, b, sb, t);
+        __syncthreads();
+        gather<C, s>(v, b, sb, t);
+        twist_and_dft<C, s>(v, t, tw, tc);
+        rest_stages_in_ring<C, s + 1>(v, b, sb, t, tw, tc);
+    }
+}
+
+// The bulk-copy ring kernel without exchange buffers of its own (XB = -1):
+// a tile arrives in ring slot k by bulk copy (TMA), stage 0 reads it from
+// there, and every later exchange (and the tensor-core A operand) reuses slot
+// k.  Slot k is refilled at the first barrier of the next tile, when every
+// thread is done with it, so the ring runs D-1 tiles ahead.  Shared memory is
+// the ring alone (plus the tensor-core B operand), so more blocks fit per SM.
+// Waits are bounded as in fft_stockham_ring_kernel.
+template <class C, bool INV>
+__global__ void __launch_bounds__(C::NT, C::MINB)
+    fft_stockham_slot_ring_kernel(const float2* in, float2* out, int64_t batch, const float2* __restrict__ tw,
+                                     float scale, int* err, uint64_t wait_ns, int stall) {
+    static_assert(C::kInRing, "in-ring schedules only");
+    constexpr int D = C::PIPE;
+    constexpr int TILE = C::S * C::N;
+    extern __shared__ __align__(16) float2 smem[];
+    float2* ring = smem;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(ring + D * TILE);
+    const int tid = threadIdx.x;
+    const int sl = tid / C::T;
+    const int t = tid % C::T;
+    const int sb = sl * C::N;
+    const int64_t ntiles = (batch + C::S - 1) / C::S;
+
+    auto issue = [&](int slot, int64_t tile) {  // thread 0 only
+        const int64_t first = tile * C::S;
+        const int64_t left = batch - first;
+        const uint32_t bytes = (uint32_t)((left < C::S ? left : C::S) * C::N * 8);
+        mbar_arrive_expect_tx(&bars[slot], bytes);
+        bulk_copy_g2s(ring + slot * TILE, in + first * C::N, bytes, &bars[slot]);
+    };
+    if (tid == 0) {
+        for (int d = 0; d < D; ++d) mbar_init(&bars[d], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    // stall != 0 is the failure-detection test mode: nothing is issued, so
+    // every wait below runs out, records FFT_ERR_TIMEOUT and the kernel ends
+    if (tid == 0 && !stall) {
+        for (int d = 0; d < D; ++d) {
+            const int64_t tile = blockIdx.x + (int64_t)d * gridDim.x;
+            if (tile < ntiles) issue(d, tile);
+        }
+    }
+    TcCtx tc;
+    if constexpr (C::TC != 0) tc_setup<C>(tc, reinterpret_cast<unsigned char*>(smem) + C::kTcOffset, err, wait_ns);
+    tc.stall = stall != 0;
+    bool dead = false;
+    if (stall) {  // wait for a phase nothing will complete: must give up after wait_ns
+        if (!mbar_wait_bounded(&bars[0], 0, wait_ns)) atomicCAS(err, 0, kErrTimeout);
+        dead = true;
+    }
+    int64_t it = 0;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+        const int slot = (int)(it % D);
+        const uint32_t parity = (uint32_t)((it / D) & 1);
+        if (!dead && !mbar_wait_bounded(&bars[slot], parity, wait_ns)) {
+            dead = true;
+            atomicCAS(err, 0, kErrTimeout);
+        }
+        float2* b = ring + slot * TILE;
+        if constexpr (C::kAInRing) tc.a = reinterpret_cast<unsigned char*>(b);
+        const int64_t sig = tile * C::S + sl;
+        float2 v[C::E];
+        gather_tile<C, INV>(v, b, sb, t);
+        twist_and_dft<C, 0>(v, t, tw, tc);
+        // order this thread's generic accesses of the previous tile's slot
+        // before the bulk copy that refills it, then one barrier: every thread
+        // is done with that slot and has read this tile's stage-0 inputs
+        fence_proxy_async_smem();
+        __syncthreads();
+        if (tid == 0 && it > 0 && !dead && !stall) {
+            const int64_t next = tile + (int64_t)(D - 1) * gridDim.x;
+            if (next < ntiles) issue((int)((it - 1) % D), next);
+        }
+        scatter<C, 0>(v, b, sb, t);
+        __syncthreads();
+        gather<C, 1>(v, b, sb, t);
+        twist_and_dft<C, 1>(v, t, tw, tc);
+        rest_stages_in_ring<C, 2>(v, b, sb, t, tw, tc);
         const bool active = sig < batch && !dead && !tc.dead;
         store_last<C, INV>(v, out + sig * C::N, t, active, scale);
     }

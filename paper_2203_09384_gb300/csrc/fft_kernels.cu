@@ -47,7 +47,10 @@ static KernelEntry generic_entry(int variant) {
     e.tc = C::TC;
     e.tmem_cols = C::TC ? C::kTcCols : 0;
     e.twiddles = C::kTwiddles;
-    if constexpr (C::PIPE > 0) {
+    if constexpr (C::kInRing) {
+        e.kernel_fwd = reinterpret_cast<const void*>(&fft_stockham_slot_ring_kernel<C, false>);
+        e.kernel_inv = reinterpret_cast<const void*>(&fft_stockham_slot_ring_kernel<C, true>);
+    } else if constexpr (C::PIPE > 0) {
         e.kernel_fwd = reinterpret_cast<const void*>(&fft_stockham_ring_kernel<C, false>);
         e.kernel_inv = reinterpret_cast<const void*>(&fft_stockham_ring_kernel<C, true>);
     } else {

@@ -21,12 +21,18 @@ from paper_2203_09384_gb300 import _abi  # noqa: E402
 TIMEOUT = _abi.STATUS_CODE["FFT_ERR_TIMEOUT"]
 
 
-@pytest.mark.parametrize("n,dtype", [(2048, "c64"), (1024, "c64"), (256, "tc_f16"), (2048, "tc_bf16")])
-def test_bounded_wait_reports_timeout(n, dtype):
+# (n, dtype, schedule variant or None for the default).  At N = 1024 / 2048
+# the default tensor-core schedules and variants 10 (FP32) and 11 (FP16) are
+# ring kernels that exchange inside the ring slot; variant 13 is the ring
+# kernel with one separate exchange buffer.
+@pytest.mark.parametrize("n,dtype,variant", [(2048, "c64", None), (1024, "c64", None), (256, "tc_f16", None),
+                                             (2048, "tc_bf16", None), (2048, "c64", 10), (1024, "tc_f16", 11),
+                                             (2048, "tc_f16", 13)])
+def test_bounded_wait_reports_timeout(n, dtype, variant):
     batch = 4 * 152 + 3
     x = synth.uniform(batch, n, seed=1).cuda()
     out = torch.zeros_like(x)
-    plan = gb.Plan(n, batch, dtype=dtype, extra_flags=gb.FFT_FLAG_TEST_STALL)
+    plan = gb.Plan(n, batch, dtype=dtype, variant=variant, extra_flags=gb.FFT_FLAG_TEST_STALL)
     info = plan.info()
     assert info.kernel_kind == 2 or info.tc != 0  # a kernel with device-side waits
     plan.set_wait_limit(1_000_000)  # 1 ms
@@ -37,7 +43,7 @@ def test_bounded_wait_reports_timeout(n, dtype):
     assert torch.count_nonzero(out) == 0  # nothing was stored
     plan.close()
     # the context is still good: a normal plan gives the right answer
-    good = gb.Plan(n, batch, dtype=dtype)
+    good = gb.Plan(n, batch, dtype=dtype, variant=variant)
     y = good.execute(x)
     torch.cuda.synchronize()
     assert good.error() == 0

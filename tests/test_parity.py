@@ -81,6 +81,54 @@ def test_every_length_and_schedule(n, variant, inverse):
         assert max_rel_l2(to_np(ys), oracle_of(xs, inverse)) <= FP32_TOL
 
 
+def _ring_candidates():
+    """Every non-complex32 schedule of the lengths that have bulk-copy-ring
+    schedules (whether a schedule uses the ring is known only from a plan)."""
+    out = []
+    for n in (128, 256, 1024, 2048):
+        for v in range(gb.fft_variant_count(n)):
+            dt = gb.fft_variant_dtype(n, v)
+            if dt != gb.FFT_C32:
+                out.append((n, v, gb.DTYPE_NAMES[dt]))
+    return out
+
+
+@pytest.mark.parametrize("n,variant,dtype", _ring_candidates())
+def test_ring_schedules_wrap_their_ring(n, variant, dtype):
+    """Every block of a bulk-copy-ring schedule goes round its ring of D slots
+    more than twice (slot reuse, refills, mbarrier phase flips) and the batch
+    ends on a ragged tile; the last tiles, first signals and a seeded sample
+    are checked against the oracle."""
+    probe = gb.Plan(n, 2 ** 22 // n, dtype=dtype, variant=variant)
+    info = probe.info()
+    probe.close()
+    if info.pipeline == 0:
+        pytest.skip("schedule without a bulk-copy ring")
+    resident, s = info.grid, info.signals_per_block  # the grid is capped at the resident blocks
+    batch = resident * s * (2 * info.pipeline + 1) + s // 2 + 1
+    if dtype == "c64":
+        x = synth.uniform(batch, n, seed=300 + variant, device="cuda")
+        tol = FP32_TOL
+    else:
+        x, _ = synth.scaled_normal(batch, n, seed=300 + variant)
+        x = x.cuda()
+        tol = 5e-3
+    for inverse in (False, True):
+        plan = gb.Plan(n, batch, inverse=inverse, dtype=dtype, variant=variant)
+        assert plan.info().grid == resident
+        out = plan.execute(x)
+        torch.cuda.synchronize()
+        assert plan.error() == 0
+        plan.close()
+        rng = np.random.default_rng(variant)
+        idx = np.unique(np.concatenate([np.arange(4), np.arange(batch - 2 * s - 64, batch),
+                                        rng.integers(0, batch, 256)]))
+        ti = torch.from_numpy(idx).cuda()
+        xs = x.index_select(0, ti).cpu()
+        got = to_np(out.index_select(0, ti))
+        assert max_rel_l2(got, oracle_of(xs, inverse)) <= tol, (n, variant, dtype, inverse)
+
+
 @pytest.mark.parametrize("n", [2 ** k for k in range(3, 12)])
 def test_paper_ramp(n):
     """The paper's input f(x) = x (Sec. 6) against its closed-form DFT."""
