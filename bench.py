@@ -550,6 +550,41 @@ def run_ours(args):
     return 0
 
 
+def write_traffic(csv_path: str, elems: int) -> None:
+    """Write profiles/traffic.json from an ncu CSV log of one forward launch per
+    length in sweep order (dram__bytes_read.sum and dram__bytes_write.sum),
+    scaled to the benchmark's 2^28 elements per launch when captured smaller,
+    with the hash of the kernel sources it describes."""
+    import csv
+
+    per_id = {}
+    order = []
+    with open(csv_path) as f:
+        rows = [r for r in csv.reader(line for line in f if not line.startswith("=="))]
+    hdr = rows[0]
+    i_id, i_name, i_val = hdr.index("ID"), hdr.index("Metric Name"), hdr.index("Metric Value")
+    i_unit = hdr.index("Metric Unit")
+    scale = {"byte": 1.0, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9}
+    for r in rows[1:]:
+        if len(r) <= i_val or r[i_name] not in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
+            continue
+        if r[i_id] not in per_id:
+            per_id[r[i_id]] = 0.0
+            order.append(r[i_id])
+        per_id[r[i_id]] += float(r[i_val].replace(",", "")) * scale[r[i_unit]]
+    if len(order) != len(LOG2NS):
+        raise SystemExit(f"expected {len(LOG2NS)} launches, found {len(order)}")
+    factor = ELEMS / elems
+    out = {"source_hash": kernel_source_hash(), "captured_elements": elems, "scaled_to_elements": ELEMS,
+           "note": "dram__bytes_read.sum + dram__bytes_write.sum of one forward launch per length"
+                   + (f", times {factor:g} (traffic grows in proportion to the elements)" if factor != 1 else ""),
+           "bytes_per_launch": {str(2 ** k): per_id[i] * factor for k, i in zip(LOG2NS, order)}}
+    with open(os.path.join(ROOT, "profiles", "traffic.json"), "w") as f:
+        json.dump(out, f, indent=1)
+        f.write("\n")
+    print(json.dumps(out["bytes_per_launch"]))
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -564,7 +599,13 @@ def main(argv=None):
     ap.add_argument("--elems", type=int, default=0, help="elements per length (profiling runs)")
     ap.add_argument("--dtype", default="c64", choices=["c64", "tc_f16", "tc_bf16", "c32"],
                     help="arithmetic / storage of the sweep (runs of the tensor-core and complex32 paths)")
+    ap.add_argument("--write-traffic", default="", metavar="NCU_CSV",
+                    help="write profiles/traffic.json from an ncu DRAM-bytes CSV of one sweep step "
+                         "(captured with --elems, if given) and exit")
     args = ap.parse_args(argv)
+    if args.write_traffic:
+        write_traffic(args.write_traffic, args.elems or ELEMS)
+        return 0
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     if args.impl == "reference":

@@ -321,6 +321,28 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 // status code written to the plan's error word by a wait that gave up
 constexpr int kErrTimeout = 8;
 
+// Bulk copies that thread 0 issued into ring slots and has not yet seen
+// complete (at most one per slot).  A block whose wait gave up stops waiting
+// and finishes its loop; before it exits, thread 0 waits (bounded) for these,
+// so that no copy lands in shared memory after the block is gone.
+struct RingInFlight {
+    uint32_t pending = 0;  // bit d: slot d's latest copy not yet seen complete
+    uint32_t parity = 0;   // bit d: mbarrier phase parity of that copy
+    __device__ __forceinline__ void issued(int d, uint32_t phase_parity) {
+        pending |= 1u << d;
+        parity = (parity & ~(1u << d)) | ((phase_parity & 1u) << d);
+    }
+    __device__ __forceinline__ void completed(int d) { pending &= ~(1u << d); }
+    __device__ __forceinline__ void drain(uint64_t* bars, uint64_t limit_ns) {
+        for (int d = 0; pending != 0 && d < 32; ++d) {
+            if (pending & (1u << d)) {
+                mbar_wait_bounded(&bars[d], (parity >> d) & 1u, limit_ns);
+                pending &= ~(1u << d);
+            }
+        }
+    }
+};
+
 // ---------------------------------------------------------------------------
 // Compile-time schedule
 // ---------------------------------------------------------------------------
@@ -420,8 +442,9 @@ struct TcCtx {
     uint64_t* bar = nullptr;
     int* err = nullptr;
     uint64_t wait_ns = 0;
-    bool dead = false;   // a bounded wait gave up: stop waiting, finish
-    bool stall = false;  // failure-detection test mode: issue no MMA
+    int mma_pending = -1;  // thread 0: parity of an MMA phase it gave up waiting for
+    bool dead = false;     // a bounded wait gave up: stop waiting, issue nothing, finish
+    bool stall = false;    // failure-detection test mode: issue no MMA
 };
 
 __device__ __forceinline__ uint64_t umma_smem_desc(uint32_t saddr) {
@@ -513,6 +536,9 @@ __device__ __forceinline__ void tc_setup(TcCtx& tc, unsigned char* base, int* er
 
 template <class C>
 __device__ __forceinline__ void tc_teardown(TcCtx& tc) {
+    // an MMA whose completion thread 0 gave up on may still write TMEM: wait
+    // for it (bounded) before the columns are freed
+    if (threadIdx.x == 0 && tc.mma_pending >= 0) mbar_wait_bounded(tc.bar, (uint32_t)tc.mma_pending, tc.wait_ns);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if ((threadIdx.x >> 5) == 0) {
@@ -575,7 +601,8 @@ __device__ __forceinline__ void tc_dft16(float2* v, TcCtx& tc) {
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (tid == 0 && !tc.stall) {
+    const bool issuer = tid == 0 && !tc.stall && !tc.dead;
+    if (issuer) {
         const uint32_t idesc = umma_idesc<C::TC>();
         const uint32_t a0 = smem_u32(tc.a), b0 = smem_u32(tc.b);
 #pragma unroll
@@ -597,6 +624,7 @@ __device__ __forceinline__ void tc_dft16(float2* v, TcCtx& tc) {
     }
     if (!tc.dead && !mbar_wait_bounded(tc.bar, tc.phase, tc.wait_ns)) {
         tc.dead = true;
+        if (issuer) tc.mma_pending = (int)tc.phase;
         atomicCAS(tc.err, 0, kErrTimeout);
     }
     tc.phase ^= 1;
@@ -836,12 +864,17 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
     const int sb = sl * C::N;
     const int64_t ntiles = (batch + C::S - 1) / C::S;
 
-    auto issue = [&](int slot, int64_t tile) {  // thread 0 only
+    RingInFlight inflight;  // thread 0's copies in flight
+    // copy the tile of the block's iteration `j` into slot j mod D (thread 0 only)
+    auto issue = [&](int64_t j) {
+        const int slot = (int)(j % D);
+        const int64_t tile = blockIdx.x + j * gridDim.x;
         const int64_t first = tile * C::S;
         const int64_t left = batch - first;
         const uint32_t bytes = (uint32_t)((left < C::S ? left : C::S) * C::N * 8);
         mbar_arrive_expect_tx(&bars[slot], bytes);
         bulk_copy_g2s(ring + slot * TILE, in + first * C::N, bytes, &bars[slot]);
+        inflight.issued(slot, (uint32_t)((j / D) & 1));
     };
     if (tid == 0) {
         for (int d = 0; d < D; ++d) mbar_init(&bars[d], 1);
@@ -851,10 +884,8 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
     // stall != 0 is the failure-detection test mode: nothing is issued, so
     // every wait below runs out, records FFT_ERR_TIMEOUT and the kernel ends
     if (tid == 0 && !stall) {
-        for (int d = 0; d < D; ++d) {
-            const int64_t tile = blockIdx.x + (int64_t)d * gridDim.x;
-            if (tile < ntiles) issue(d, tile);
-        }
+        for (int d = 0; d < D; ++d)
+            if (blockIdx.x + (int64_t)d * gridDim.x < ntiles) issue(d);
     }
     TcCtx tc;
     if constexpr (C::TC != 0) tc_setup<C>(tc, reinterpret_cast<unsigned char*>(smem) + C::kTcOffset, err, wait_ns);
@@ -869,9 +900,13 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
         const int slot = (int)(it % D);
         const uint32_t parity = (uint32_t)((it / D) & 1);
-        if (!dead && !mbar_wait_bounded(&bars[slot], parity, wait_ns)) {
-            dead = true;
-            atomicCAS(err, 0, kErrTimeout);
+        if (!dead) {
+            if (mbar_wait_bounded(&bars[slot], parity, wait_ns)) {
+                inflight.completed(slot);
+            } else {
+                dead = true;
+                atomicCAS(err, 0, kErrTimeout);
+            }
         }
         const int64_t sig = tile * C::S + sl;
         float2 v[C::E];
@@ -882,10 +917,9 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
         scatter<C, 0>(v, b, sb, t);
         __syncthreads();  // every thread is done with ring[slot]
         if (tid == 0 && !dead && !stall) {
-            const int64_t next = tile + (int64_t)D * gridDim.x;
-            if (next < ntiles) {
+            if (tile + (int64_t)D * gridDim.x < ntiles) {
                 fence_proxy_async_smem();
-                issue(slot, next);
+                issue(it + D);
             }
         }
         gather<C, 1>(v, b, sb, t);
@@ -895,6 +929,7 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
         const bool active = sig < batch && !dead && !tc.dead;
         store_last<C, INV>(v, out + sig * C::N, t, active, scale);
     }
+    if (tid == 0) inflight.drain(bars, wait_ns);  // copies in flight after a wait gave up
     if constexpr (C::TC != 0) tc_teardown<C>(tc);
 }
 
@@ -941,12 +976,17 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
     const int sb = sl * C::N;
     const int64_t ntiles = (batch + C::S - 1) / C::S;
 
-    auto issue = [&](int slot, int64_t tile) {  // thread 0 only
+    RingInFlight inflight;  // thread 0's copies in flight
+    // copy the tile of the block's iteration `j` into slot j mod D (thread 0 only)
+    auto issue = [&](int64_t j) {
+        const int slot = (int)(j % D);
+        const int64_t tile = blockIdx.x + j * gridDim.x;
         const int64_t first = tile * C::S;
         const int64_t left = batch - first;
         const uint32_t bytes = (uint32_t)((left < C::S ? left : C::S) * C::N * 8);
         mbar_arrive_expect_tx(&bars[slot], bytes);
         bulk_copy_g2s(ring + slot * TILE, in + first * C::N, bytes, &bars[slot]);
+        inflight.issued(slot, (uint32_t)((j / D) & 1));
     };
     if (tid == 0) {
         for (int d = 0; d < D; ++d) mbar_init(&bars[d], 1);
@@ -956,10 +996,8 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
     // stall != 0 is the failure-detection test mode: nothing is issued, so
     // every wait below runs out, records FFT_ERR_TIMEOUT and the kernel ends
     if (tid == 0 && !stall) {
-        for (int d = 0; d < D; ++d) {
-            const int64_t tile = blockIdx.x + (int64_t)d * gridDim.x;
-            if (tile < ntiles) issue(d, tile);
-        }
+        for (int d = 0; d < D; ++d)
+            if (blockIdx.x + (int64_t)d * gridDim.x < ntiles) issue(d);
     }
     TcCtx tc;
     if constexpr (C::TC != 0) tc_setup<C>(tc, reinterpret_cast<unsigned char*>(smem) + C::kTcOffset, err, wait_ns);
@@ -973,9 +1011,13 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
         const int slot = (int)(it % D);
         const uint32_t parity = (uint32_t)((it / D) & 1);
-        if (!dead && !mbar_wait_bounded(&bars[slot], parity, wait_ns)) {
-            dead = true;
-            atomicCAS(err, 0, kErrTimeout);
+        if (!dead) {
+            if (mbar_wait_bounded(&bars[slot], parity, wait_ns)) {
+                inflight.completed(slot);
+            } else {
+                dead = true;
+                atomicCAS(err, 0, kErrTimeout);
+            }
         }
         float2* b = ring + slot * TILE;
         if constexpr (C::kAInRing) tc.a = reinterpret_cast<unsigned char*>(b);
@@ -989,8 +1031,7 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
         fence_proxy_async_smem();
         __syncthreads();
         if (tid == 0 && it > 0 && !dead && !stall) {
-            const int64_t next = tile + (int64_t)(D - 1) * gridDim.x;
-            if (next < ntiles) issue((int)((it - 1) % D), next);
+            if (tile + (int64_t)(D - 1) * gridDim.x < ntiles) issue(it - 1 + D);
         }
         scatter<C, 0>(v, b, sb, t);
         __syncthreads();
@@ -1000,6 +1041,7 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
         const bool active = sig < batch && !dead && !tc.dead;
         store_last<C, INV>(v, out + sig * C::N, t, active, scale);
     }
+    if (tid == 0) inflight.drain(bars, wait_ns);  // copies in flight after a wait gave up
     if constexpr (C::TC != 0) tc_teardown<C>(tc);
 }
 
@@ -1276,12 +1318,17 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
     const int ls = log2_pow2(scale);
     const int64_t ntiles = (batch + C::S - 1) / C::S;
 
-    auto issue = [&](int slot, int64_t tile) {  // thread 0 only
+    RingInFlight inflight;  // thread 0's copies in flight
+    // copy the tile of the block's iteration `j` into slot j mod D (thread 0 only)
+    auto issue = [&](int64_t j) {
+        const int slot = (int)(j % D);
+        const int64_t tile = blockIdx.x + j * gridDim.x;
         const int64_t first = tile * C::S;
         const int64_t left = batch - first;
         const uint32_t bytes = (uint32_t)((left < C::S ? left : C::S) * C::N * 4);
         mbar_arrive_expect_tx(&bars[slot], bytes);
         bulk_copy_g2s(ring + slot * TILE, in + first * C::N, bytes, &bars[slot]);
+        inflight.issued(slot, (uint32_t)((j / D) & 1));
     };
     if (tid == 0) {
         for (int d = 0; d < D; ++d) mbar_init(&bars[d], 1);
@@ -1289,10 +1336,8 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
     }
     __syncthreads();
     if (tid == 0 && !stall) {
-        for (int d = 0; d < D; ++d) {
-            const int64_t tile = blockIdx.x + (int64_t)d * gridDim.x;
-            if (tile < ntiles) issue(d, tile);
-        }
+        for (int d = 0; d < D; ++d)
+            if (blockIdx.x + (int64_t)d * gridDim.x < ntiles) issue(d);
     }
     TcCtx tc;  // FP32 butterflies only
     bool dead = false;
@@ -1308,9 +1353,13 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
         const int64_t sig = tile * C::S + sl;
         const bool in_range = sig < batch;
         const int ein = in_range ? (int)in_exp[sig] : 0;
-        if (!dead && !mbar_wait_bounded(&bars[slot], parity, wait_ns)) {
-            dead = true;
-            atomicCAS(err, 0, kErrTimeout);
+        if (!dead) {
+            if (mbar_wait_bounded(&bars[slot], parity, wait_ns)) {
+                inflight.completed(slot);
+            } else {
+                dead = true;
+                atomicCAS(err, 0, kErrTimeout);
+            }
         }
         float2 v[C::E];
         gather_tile_c32<C, INV>(v, ring + slot * TILE, sb, t);
@@ -1320,10 +1369,9 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
         scatter<C, 0>(v, b, sb, t);
         __syncthreads();  // every thread is done with ring[slot]
         if (tid == 0 && !dead && !stall) {
-            const int64_t next = tile + (int64_t)D * gridDim.x;
-            if (next < ntiles) {
+            if (tile + (int64_t)D * gridDim.x < ntiles) {
                 fence_proxy_async_smem();
-                issue(slot, next);
+                issue(it + D);
             }
         }
         gather<C, 1>(v, b, sb, t);
@@ -1333,6 +1381,7 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
         const C32Out o = c32_out_scale(c32_signal_max<C>(v, red), ein, ls);
         store_last_c32<C, INV>(v, out + sig * C::N, out_exp + sig, t, in_range && !dead, o);
     }
+    if (tid == 0) inflight.drain(bars, wait_ns);  // copies in flight after a wait gave up
 }
 
 // complex32, N = 2..32: one thread owns a whole signal, as in

@@ -257,10 +257,14 @@ __global__ void __launch_bounds__(kRaggedThreads, 3) fft_ragged_ring_kernel(Ragg
         fence_mbar_init();
     }
     __syncthreads();
+    RingInFlight inflight;  // thread 0's view of warp 0's copies in flight
     if (tid < 32) {
         for (int d = 0; d < 2; ++d) {
             const int it = (int)blockIdx.x + d * grid;
-            if (it < a.n_items) ragged_issue(a, ring + d * kRingTile, &bars[d], it);
+            if (it < a.n_items) {
+                ragged_issue(a, ring + d * kRingTile, &bars[d], it);
+                inflight.issued(d, 0);
+            }
         }
     }
     bool dead = false;
@@ -268,13 +272,21 @@ __global__ void __launch_bounds__(kRaggedThreads, 3) fft_ragged_ring_kernel(Ragg
     for (int it = blockIdx.x; it < a.n_items; it += grid, ++k) {
         const int slot = k & 1;
         const uint32_t parity = (uint32_t)((k >> 1) & 1);
-        if (!dead && !mbar_wait_bounded(&bars[slot], parity, a.wait_ns)) {
-            dead = true;
-            atomicCAS(a.err, 0, kErrTimeout);
+        if (!dead) {
+            if (mbar_wait_bounded(&bars[slot], parity, a.wait_ns)) {
+                inflight.completed(slot);
+            } else {
+                dead = true;
+                atomicCAS(a.err, 0, kErrTimeout);
+            }
         }
         const RaggedItem w = a.items[it];
         const int nx = it + 2 * grid;
-        const int refill = (nx < a.n_items && !dead) ? nx : -1;
+        // warp 0 issues the refill together (one lane sets the byte count,
+        // all lanes copy), so it decides once: no refill if any lane gave up
+        const bool wdead = __any_sync(0xffffffffu, dead);
+        const int refill = (nx < a.n_items && !wdead) ? nx : -1;
+        if (refill >= 0) inflight.issued(slot, (uint32_t)(((k + 2) >> 1) & 1));
         switch (w.log2n) {
 #define GBFFT_RRING(L)                                                                                        \
     case L: {                                                                                                 \
@@ -290,6 +302,7 @@ __global__ void __launch_bounds__(kRaggedThreads, 3) fft_ragged_ring_kernel(Ragg
         }
         __syncthreads();  // the next item reuses shared memory with another shape
     }
+    if (tid == 0) inflight.drain(bars, a.wait_ns);  // copies in flight after a wait gave up
 }
 
 // ---------------------------------------------------------------------------
