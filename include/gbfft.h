@@ -114,10 +114,10 @@ GBFFT_API fft_status_t fft_plan_create(int64_t n, int64_t batch, int direction, 
  * buffers later passed to fft_execute; every length must be a power of two in
  * [2, 2048] and offsets_host[0] must be even (so every signal starts 16-byte
  * aligned).  The plan buckets the signals by length into tiles and uploads a
- * device work list; fft_execute then clears the plan's work counter with a
- * memset node and launches ONE persistent kernel whose blocks take tiles from
- * the list (graph-capturable).  Because of that counter, a ragged plan must
- * not be executed on two streams at once.  flags: FFT_FLAG_UNNORMALIZED,
+ * device work list; fft_execute then launches ONE persistent kernel whose
+ * blocks take tiles from the list (graph-capturable).  Variants that share
+ * the tiles through a work counter clear it first with a memset node; because
+ * of that counter, a ragged plan must not be executed on two streams at once.  flags: FFT_FLAG_UNNORMALIZED,
  * FFT_FLAG_SCALE_FORWARD, FFT_FLAG_VARIANT(k) with k < fft_ragged_variant_count().
  * Errors: FFT_ERR_INVALID_SIZE (a length), FFT_ERR_INVALID_VALUE, FFT_ERR_MISALIGNED
  * (odd offsets_host[0]), FFT_ERR_ALLOC, FFT_ERR_CUDA, FFT_ERR_NO_DEVICE.

@@ -4,14 +4,17 @@
 // Plan time (host): signals are bucketed by length; every bucket is cut into
 // tiles of S_N signals (the same per-length schedules as the uniform path,
 // re-shaped so that every length runs in a 256-thread block), and the tiles
-// become a device work list ordered from the longest length down.  Execute:
-// a memset node clears the work counter, then the kernel's blocks pull work
-// items with one atomicAdd each until the list is exhausted.  Both steps are
-// stream-ordered, so the pair can be captured in a CUDA graph.
+// become a device work list ordered from the longest length down.
 //
-// Two schedule variants are compiled: V0 keeps 16 complex elements per thread
-// for N >= 32 (fewest exchanges), V1 keeps 8 (fewer registers, more resident
-// blocks, finer tiles).  The autotuner picks between them per workload.
+// Five variants are compiled.  Bit 0 of variants 0..3 picks the schedule set:
+// set 0 keeps 16 complex elements per thread for N >= 32 (fewest exchanges),
+// set 1 keeps 8 (fewer registers, more resident blocks, finer tiles).  Bit 1
+// picks how blocks get work: 0 = a shared counter (one atomicAdd per item;
+// fft_execute clears it with a memset node first), 1 = static round robin with
+// the next item's descriptor prefetched.  Variant 4 runs set 1 with a bulk-copy
+// (TMA) ring that keeps the next item's signals in flight.  Every step is
+// stream-ordered, so an execute can be captured in a CUDA graph.  The
+// autotuner picks a variant per workload.
 #include <cuda_runtime.h>
 
 #include <stdint.h>
@@ -526,7 +529,9 @@ fft_status_t ragged_execute(RaggedState* st, const void* in, void* out, void* st
     const uintptr_t a = (uintptr_t)in, b = (uintptr_t)out;
     if (a != b && a + lo < b + hi && b + lo < a + hi) return FFT_ERR_OVERLAP;
     cudaStream_t s = (cudaStream_t)stream;
-    if (cudaMemsetAsync(st->args.counter, 0, sizeof(unsigned int), s) != cudaSuccess) {
+    // only the work-counter variants (bit 1 clear, not the ring) read the counter
+    const bool uses_counter = st->variant != kRingVariant && ((st->variant >> 1) & 1) == 0;
+    if (uses_counter && cudaMemsetAsync(st->args.counter, 0, sizeof(unsigned int), s) != cudaSuccess) {
         cudaGetLastError();
         return FFT_ERR_CUDA;
     }

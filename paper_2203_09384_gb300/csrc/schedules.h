@@ -59,7 +59,7 @@
     GX(10, 12, 16, 2, 8, 16, 8, 0, 5, 2, 2, -1, 0) \
     GX(10, 13, 16, 2, 8, 16, 8, 0, 4, 2, 1, 1, 0) \
     GX(10, 14, 16, 2, 8, 16, 8, 0, 4, 2, 2, 1, 0) \
-    GX(11, 0, 16, 1, 8, 16, 16, 0, 3, 2, 0, 0, 2) \
+    GX(11, 0, 16, 1, 8, 16, 16, 0, 5, 2, 0, -1, 2) \
     GX(11, 1, 16, 1, 8, 16, 16, 0, 1, 0, 0, 0, 0) \
     GX(11, 2, 16, 1, 8, 16, 16, 0, 2, 3, 0, 0, 0) \
     GX(11, 3, 16, 2, 8, 16, 16, 0, 1, 2, 0, 0, 0) \
@@ -67,7 +67,7 @@
     GX(11, 5, 16, 1, 8, 16, 16, 0, 5, 2, 2, -2, 0) \
     GX(11, 6, 16, 1, 8, 16, 16, 0, 3, 2, 1, 0, 0) \
     GX(11, 7, 16, 1, 8, 16, 16, 0, 3, 2, 2, 0, 0) \
-    GX(11, 10, 16, 1, 8, 16, 16, 0, 5, 2, 0, -1, 2) \
+    GX(11, 10, 16, 1, 8, 16, 16, 0, 3, 2, 0, 0, 2) \
     GX(11, 11, 16, 1, 8, 16, 16, 0, 5, 2, 1, -1, 0) \
     GX(11, 12, 16, 1, 8, 16, 16, 0, 5, 2, 2, -1, 0) \
     GX(11, 13, 16, 1, 8, 16, 16, 0, 4, 2, 1, 1, 0) \

@@ -21,10 +21,11 @@ from paper_2203_09384_gb300 import _abi  # noqa: E402
 TIMEOUT = _abi.STATUS_CODE["FFT_ERR_TIMEOUT"]
 
 
-# (n, dtype, schedule variant or None for the default).  At N = 1024 / 2048
-# the default tensor-core schedules and variants 10 (FP32) and 11 (FP16) are
-# ring kernels that exchange inside the ring slot; variant 13 is the ring
-# kernel with one separate exchange buffer.
+# (n, dtype, schedule variant or None for the default).  At N = 2048 the
+# default FP32 schedule, at N = 1024 / 2048 the default tensor-core schedules
+# and variant 11 (FP16) are ring kernels that exchange inside the ring slot;
+# variant 10 of N = 2048 is the ring kernel with two exchange buffers and
+# variant 13 the one with one separate exchange buffer.
 @pytest.mark.parametrize("n,dtype,variant", [(2048, "c64", None), (1024, "c64", None), (256, "tc_f16", None),
                                              (2048, "tc_bf16", None), (2048, "c64", 10), (1024, "tc_f16", 11),
                                              (2048, "tc_f16", 13)])

@@ -60,7 +60,7 @@ def test_ragged_workload_in_a_cuda_graph(workload, variant):
     g = plan.capture(xd, out)
     out.fill_(float("nan"))
     g.replay()
-    g.replay()  # the captured memset node resets the work counter every replay
+    g.replay()  # replays again: counter variants reset their work counter in a memset node
     torch.cuda.synchronize()
     got = out.cpu().numpy().astype(np.complex128)
     assert per_signal_max_err(got, want, offsets) <= FP32_TOL
