@@ -12,7 +12,9 @@
 // picks how blocks get work: 0 = a shared counter (one atomicAdd per item;
 // fft_execute clears it with a memset node first), 1 = static round robin with
 // the next item's descriptor prefetched.  Variant 4 runs set 1 with a bulk-copy
-// (TMA) ring that keeps the next item's signals in flight.  Every step is
+// (TMA) ring that keeps the next item's signals in flight; variant 5 runs set
+// 0 in ring slots that a producer warp fills (exchanges inside the slot).
+// Every step is
 // stream-ordered, so an execute can be captured in a CUDA graph.  The
 // autotuner picks a variant per workload.
 #include <cuda_runtime.h>
@@ -89,9 +91,15 @@ GBFFT_RCFG(1, 11, 8, 1, 4, 8, 8, 8)
 #undef GBFFT_RCFG
 
 // variants 0..3: bit 0 schedule set, bit 1 work distribution; variant 4: the
-// schedule set 1 shapes fed by a bulk-copy (TMA) prefetch ring
-constexpr int kRaggedVariants = 5;
+// schedule set 1 shapes fed by a bulk-copy (TMA) prefetch ring; variants 5..7:
+// set 0 shapes in ring slots filled by a producer warp (5: 256 compute threads
+// and 2 slots; 6 / 7: 128 compute threads, half the signals per tile, 2 / 3
+// slots)
+constexpr int kRaggedVariants = 8;
 constexpr int kRingVariant = 4;
+constexpr int kFirstProducerVariant = 5;
+constexpr int kDefaultRaggedVariant = 6;  // measured fastest on the mixed-length workload
+__host__ __device__ constexpr bool is_producer_variant(int v) { return v >= kFirstProducerVariant; }
 
 // the ring variant's per-length schedules: set 1 with a 2-slot ring
 template <int L>
@@ -101,6 +109,23 @@ struct RingCfg {
 };
 constexpr int kRingTile = 2048;  // complex elements per item (S * N) at most
 constexpr int kRaggedThreads = 256;
+
+// the producer variants' per-length schedules for NTC compute threads: set 0
+// radices and elements per thread, NTC / 256 of its signals per tile, stage 0
+// read from the ring slot and every exchange inside it (XB = -1)
+template <int NTC, int L>
+struct SlotCfg {
+    using B = typename RCfg<0, L>::type;
+    using type = Cfg<L, B::E, B::S * NTC / kRaggedThreads, B::radix(0), B::radix(1), B::radix(2), B::radix(3), 2, 2,
+                     0, -1, 0>;
+    static_assert(type::NT == NTC, "one tile per compute group");
+};
+template <int NTC>
+struct SlotShape {
+    static constexpr int kTile = NTC * 16;        // complex elements per tile (S * N) at most
+    static constexpr int kThreads = NTC + 32;     // compute threads + the producer warp
+    static constexpr int kMinBlocks = NTC == 256 ? 2 : 4;
+};
 template <int V>
 struct RaggedMinBlocks {
     static constexpr int value = V == 0 ? 2 : 3;
@@ -309,6 +334,189 @@ __global__ void __launch_bounds__(kRaggedThreads, 3) fft_ragged_ring_kernel(Ragg
 }
 
 // ---------------------------------------------------------------------------
+// Variant 5: a producer warp and ring slots.  Block = 256 compute threads plus
+// one producer warp.  The producer walks the block's items (round robin) and,
+// once the compute threads have released a slot (its `empty` mbarrier), copies
+// the next item's signals into it with one bulk copy per signal, completing on
+// the slot's `full` mbarrier.  The compute threads wait on `full`, read stage
+// 0 from the slot, exchange inside it (one named barrier per signal over the
+// threads of a signal, or a warp sync when a signal stays in one warp), release
+// the slot after the last exchange and store the result from registers.  The dependent
+// descriptor and offset loads of the next item are the producer's alone, so
+// they never stall the compute threads.  Every wait is bounded.
+// ---------------------------------------------------------------------------
+// Exchange barrier of one signal: its slot region is touched by its own T
+// threads only, so a signal within one warp needs a warp sync, and a signal
+// spanning warps syncs its T threads on named barrier 1 + (index of its first
+// warp); barrier 0 stays the block's.  Warps are not synchronised between
+// items, so one warp group may already run a later item (another length,
+// other signal boundaries) while another is still exchanging in an earlier
+// one.  A barrier must never see arrivals with two thread counts at once.
+// That holds because a block's items come longest first (the host sorts the
+// work list by length, and a block takes a subsequence of it), so T never
+// grows from one item to the next: a later signal that uses barrier b lies
+// inside the earlier signal that used b (both start at warp b - 1), whose
+// warps all had to complete their barriers before any of them moved on.
+// (Were T to grow, warps of a later, wider signal could arrive at b while an
+// earlier, narrower signal still used it.)
+template <class C>
+__device__ __forceinline__ void slot_sync() {
+    if constexpr (C::T <= 32) {
+        __syncwarp();
+    } else {
+        static_assert(C::T % 32 == 0 && C::NT <= 15 * 32, "whole warps; barriers 1..15");
+        constexpr int kWarps = C::T / 32;  // warps per signal
+        const int first_warp = ((int)threadIdx.x >> 5) & ~(kWarps - 1);
+        asm volatile("bar.sync %0, %1;" ::"r"(1 + first_warp), "n"(C::T) : "memory");
+    }
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+template <class C, int s>
+__device__ __forceinline__ void slot_stages(float2 (&v)[C::E], float2* b, int sb, int t, const float2* __restrict__ tw,
+                                            TcCtx& tc) {
+    if constexpr (s < C::M) {
+        slot_sync<C>();  // every reader of b (the tile, or stage s-1's gather) is done
+        scatter<C, s - 1>(v, b, sb, t);
+        slot_sync<C>();
+        gather<C, s>(v, b, sb, t);
+        twist_and_dft<C, s>(v, t, tw, tc);
+        slot_stages<C, s + 1>(v, b, sb, t, tw, tc);
+    }
+}
+
+template <class C, bool INV>
+__device__ __forceinline__ void slot_tile(const RaggedArgs& a, const RaggedItem& w, float2* slot, uint64_t* empty,
+                                          int64_t off, bool dead) {
+    static_assert(C::S * C::N <= C::NT * 16, "a tile must fit a ring slot");
+    const int tid = threadIdx.x;
+    const int sl = tid / C::T;
+    const int t = tid % C::T;
+    const bool active = sl < w.count && !dead;
+    const float2* tw = a.tw + a.tw_off[C::LOG2N];
+    const float scale = a.scale_mode ? 1.0f / (float)C::N : 1.0f;
+    TcCtx tc;  // FP32 butterflies only
+    float2 v[C::E];
+    gather_tile<C, INV>(v, slot, sl * C::N, t);
+    twist_and_dft<C, 0>(v, t, tw, tc);
+    slot_stages<C, 1>(v, slot, sl * C::N, t, tw, tc);
+    // this thread is done with the slot: order its shared-memory accesses
+    // before the producer's next bulk copy into it, then release
+    fence_proxy_async_smem();
+    mbar_arrive(empty);
+    store_last<C, INV>(v, a.out + off, t, active, scale);
+}
+
+template <int NTC>
+__device__ __forceinline__ int64_t slot_offset_for(const RaggedArgs& a, const RaggedItem& w) {
+    switch (w.log2n) {
+#define GBFFT_SOFF(L) \
+    case L: return ragged_offset<typename SlotCfg<NTC, L>::type>(a, w);
+        GBFFT_SOFF(1) GBFFT_SOFF(2) GBFFT_SOFF(3) GBFFT_SOFF(4) GBFFT_SOFF(5) GBFFT_SOFF(6)
+        GBFFT_SOFF(7) GBFFT_SOFF(8) GBFFT_SOFF(9) GBFFT_SOFF(10) GBFFT_SOFF(11)
+#undef GBFFT_SOFF
+        default: return 0;
+    }
+}
+
+// The producer warp.  Lane 0 sets each fill's byte count; every lane copies
+// signals lane, lane + 32, ...  Before it exits, lane 0 waits (bounded) for
+// the copies it issued last, so none lands after the block is gone even when
+// the compute threads gave up.
+template <int NTC, int SLOTS>
+__device__ __forceinline__ void slot_produce(const RaggedArgs& a, float2* ring, uint64_t* full, uint64_t* empty) {
+    constexpr int kSlots = SLOTS;
+    constexpr int kSlotTile = SlotShape<NTC>::kTile;
+    const int lane = threadIdx.x & 31;
+    RingInFlight inflight;  // lane 0
+    int k = 0;
+    for (int it = blockIdx.x; it < a.n_items; it += gridDim.x, ++k) {
+        const int slot = k % kSlots;
+        if (k >= kSlots) {  // the compute threads must have released the slot's previous item
+            bool ok = true;
+            if (lane == 0) {
+                ok = mbar_wait_bounded(&empty[slot], (uint32_t)((k / kSlots - 1) & 1), a.wait_ns);
+                if (ok) inflight.completed(slot);  // that item's copy was consumed
+                else atomicCAS(a.err, 0, kErrTimeout);
+            }
+            if (!__shfl_sync(0xffffffffu, ok, 0)) break;
+        }
+        const RaggedItem w = a.items[it];
+        const int n = 1 << w.log2n;
+        float2* dst = ring + slot * kSlotTile;
+        if (lane == 0) {
+            mbar_arrive_expect_tx(&full[slot], (uint32_t)(w.count * n * 8));
+            inflight.issued(slot, (uint32_t)((k / kSlots) & 1));
+        }
+        __syncwarp();
+        for (int j = lane; j < w.count; j += 32)
+            bulk_copy_g2s(dst + j * n, a.in + a.sig_off[w.first + j], (uint32_t)(n * 8), &full[slot]);
+    }
+    if (lane == 0) inflight.drain(full, a.wait_ns);
+}
+
+template <int NTC, int SLOTS, bool INV>
+__global__ void __launch_bounds__(SlotShape<NTC>::kThreads, SlotShape<NTC>::kMinBlocks)
+    fft_ragged_slot_kernel(RaggedArgs a) {
+    constexpr int kSlots = SLOTS;
+    constexpr int kSlotTile = SlotShape<NTC>::kTile;
+    extern __shared__ __align__(16) float2 smem[];
+    float2* ring = smem;  // kSlots slots of kSlotTile elements
+    uint64_t* full = reinterpret_cast<uint64_t*>(ring + kSlots * kSlotTile);
+    uint64_t* empty = full + kSlots;
+    const int tid = threadIdx.x;
+    const int grid = (int)gridDim.x;
+    if (tid == 0) {
+        for (int d = 0; d < kSlots; ++d) {
+            mbar_init(&full[d], 1);
+            mbar_init(&empty[d], NTC);
+        }
+        fence_mbar_init();
+    }
+    __syncthreads();  // the last barrier of all NTC + 32 threads
+    if (tid >= NTC) {
+        slot_produce<NTC, SLOTS>(a, ring, full, empty);
+        return;
+    }
+    int it = blockIdx.x;
+    if (it >= a.n_items) return;
+    RaggedItem w = a.items[it];
+    int64_t off = slot_offset_for<NTC>(a, w);
+    bool dead = false;
+    for (int k = 0;; ++k) {
+        const int nx = it + grid;
+        RaggedItem wn{};
+        int64_t offn = 0;
+        if (nx < a.n_items) {  // the next item's descriptor and this thread's offset, ahead of time
+            wn = a.items[nx];
+            offn = slot_offset_for<NTC>(a, wn);
+        }
+        const int slot = k % kSlots;
+        if (!dead && !mbar_wait_bounded(&full[slot], (uint32_t)((k / kSlots) & 1), a.wait_ns)) {
+            dead = true;
+            atomicCAS(a.err, 0, kErrTimeout);
+        }
+        switch (w.log2n) {
+#define GBFFT_SCASE(L)                                                                                       \
+    case L:                                                                                                  \
+        slot_tile<typename SlotCfg<NTC, L>::type, INV>(a, w, ring + slot * kSlotTile, &empty[slot], off, dead); \
+        break;
+            GBFFT_SCASE(1) GBFFT_SCASE(2) GBFFT_SCASE(3) GBFFT_SCASE(4) GBFFT_SCASE(5) GBFFT_SCASE(6)
+            GBFFT_SCASE(7) GBFFT_SCASE(8) GBFFT_SCASE(9) GBFFT_SCASE(10) GBFFT_SCASE(11)
+#undef GBFFT_SCASE
+            default: break;
+        }
+        if (nx >= a.n_items) break;
+        it = nx;
+        w = wn;
+        off = offn;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
 namespace {
@@ -365,10 +573,15 @@ struct RaggedHost {
 
 // The schedule set a variant's kernel runs: bit 0 of variants 0..3; the ring
 // variant runs set 1.  Work list, tile sizes and twiddle tables must follow it.
-int schedule_set(int v) { return v == kRingVariant ? 1 : (v & 1); }
+int schedule_set(int v) { return v == kRingVariant ? 1 : is_producer_variant(v) ? 0 : (v & 1); }
+// compute threads per block of a producer variant (0 for the others) and its ring slots
+int producer_group(int v) { return v == 5 ? 256 : is_producer_variant(v) ? 128 : 0; }
+int producer_slots(int v) { return v == 7 ? 3 : 2; }
+int ragged_threads(int v) { return is_producer_variant(v) ? producer_group(v) + 32 : kRaggedThreads; }
 
 int signals_per_tile(int v, int L) {
-    return schedule_set(v) == 0 ? RaggedHost<0>::signals_per_tile(L) : RaggedHost<1>::signals_per_tile(L);
+    const int s = schedule_set(v) == 0 ? RaggedHost<0>::signals_per_tile(L) : RaggedHost<1>::signals_per_tile(L);
+    return is_producer_variant(v) ? s * producer_group(v) / kRaggedThreads : s;  // as SlotCfg<NTC, L>
 }
 int twiddle_count(int v, int L) {
     return schedule_set(v) == 0 ? RaggedHost<0>::twiddles(L) : RaggedHost<1>::twiddles(L);
@@ -385,6 +598,15 @@ const void* ragged_kernel(int v, bool inv) {
         case 1: return RaggedHost<1>::kernel(inv);
         case 2: return RaggedHost<2>::kernel(inv);
         case 3: return RaggedHost<3>::kernel(inv);
+        case 5:
+            return inv ? reinterpret_cast<const void*>(&fft_ragged_slot_kernel<256, 2, true>)
+                       : reinterpret_cast<const void*>(&fft_ragged_slot_kernel<256, 2, false>);
+        case 6:
+            return inv ? reinterpret_cast<const void*>(&fft_ragged_slot_kernel<128, 2, true>)
+                       : reinterpret_cast<const void*>(&fft_ragged_slot_kernel<128, 2, false>);
+        case 7:
+            return inv ? reinterpret_cast<const void*>(&fft_ragged_slot_kernel<128, 3, true>)
+                       : reinterpret_cast<const void*>(&fft_ragged_slot_kernel<128, 3, false>);
         default:
             return inv ? reinterpret_cast<const void*>(&fft_ragged_ring_kernel<true>)
                        : reinterpret_cast<const void*>(&fft_ragged_ring_kernel<false>);
@@ -392,6 +614,7 @@ const void* ragged_kernel(int v, bool inv) {
 }
 int ragged_smem(int v) {
     if (v == kRingVariant) return 4 * kRingTile * (int)sizeof(float2) + 16;
+    if (is_producer_variant(v)) return producer_slots(v) * producer_group(v) * 16 * (int)sizeof(float2) + 2 * producer_slots(v) * 8;
     return schedule_set(v) == 0 ? ragged_smem_bytes<0>() : ragged_smem_bytes<1>();
 }
 
@@ -418,7 +641,7 @@ fft_status_t ragged_create(const int64_t* offsets, int64_t count, int direction,
     if (count < 0 || (count > 0 && !offsets)) return FFT_ERR_INVALID_VALUE;
     if (count > (int64_t)1 << 31) return FFT_ERR_INVALID_VALUE;
     int variant = (int)((flags & FFT_FLAG_VARIANT_MASK) >> 8) - 1;
-    if (variant < 0) variant = 0;
+    if (variant < 0) variant = kDefaultRaggedVariant;
     if (variant >= kRaggedVariants) return FFT_ERR_INVALID_VALUE;
     if (offsets && (offsets[0] < 0 || (offsets[0] & 1))) return FFT_ERR_MISALIGNED;
     std::vector<std::vector<int64_t>> buckets(GBFFT_MAX_LOG2N + 1);
@@ -438,7 +661,8 @@ fft_status_t ragged_create(const int64_t* offsets, int64_t count, int direction,
     st->begin = count > 0 ? offsets[0] : 0;
     st->end = count > 0 ? offsets[count] : 0;
 
-    // work list (longest length first) and the bucketed offsets
+    // work list (longest length first: the producer variants' named barriers
+    // rely on that order, see slot_sync) and the bucketed offsets
     std::vector<RaggedItem> items;
     std::vector<int64_t> sig;
     sig.reserve((size_t)count);
@@ -450,7 +674,8 @@ fft_status_t ragged_create(const int64_t* offsets, int64_t count, int direction,
         tw_off[L] = tw_total;
         tw_total += twiddle_count(variant, L);
         const int S = signals_per_tile(variant, L);
-        if (S < 1 || (variant == kRingVariant && (int64_t)S << L > kRingTile)) {  // a tile must fit the kernel
+        if (S < 1 || (variant == kRingVariant && (int64_t)S << L > kRingTile) ||
+            (is_producer_variant(variant) && (int64_t)S << L > (int64_t)producer_group(variant) * 16)) {  // a tile must fit the kernel
             delete st;
             return FFT_ERR_UNSUPPORTED;
         }
@@ -506,7 +731,7 @@ fft_status_t ragged_create(const int64_t* offsets, int64_t count, int direction,
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
         (st->smem > 48 * 1024 &&
          cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, st->smem) != cudaSuccess) ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kRaggedThreads, st->smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, ragged_threads(variant), st->smem) != cudaSuccess ||
         per_sm < 1) {
         cudaGetLastError();
         cudaFree(st->dmem);
@@ -530,7 +755,7 @@ fft_status_t ragged_execute(RaggedState* st, const void* in, void* out, void* st
     if (a != b && a + lo < b + hi && b + lo < a + hi) return FFT_ERR_OVERLAP;
     cudaStream_t s = (cudaStream_t)stream;
     // only the work-counter variants (bit 1 clear, not the ring) read the counter
-    const bool uses_counter = st->variant != kRingVariant && ((st->variant >> 1) & 1) == 0;
+    const bool uses_counter = st->variant < kRingVariant && ((st->variant >> 1) & 1) == 0;
     if (uses_counter && cudaMemsetAsync(st->args.counter, 0, sizeof(unsigned int), s) != cudaSuccess) {
         cudaGetLastError();
         return FFT_ERR_CUDA;
@@ -539,7 +764,8 @@ fft_status_t ragged_execute(RaggedState* st, const void* in, void* out, void* st
     args.in = static_cast<const float2*>(in);
     args.out = static_cast<float2*>(out);
     void* kargs[] = {&args};
-    if (cudaLaunchKernel(ragged_kernel(st->variant, st->inverse), dim3((unsigned)st->grid), dim3(kRaggedThreads),
+    if (cudaLaunchKernel(ragged_kernel(st->variant, st->inverse), dim3((unsigned)st->grid),
+                         dim3(ragged_threads(st->variant)),
                          kargs, (size_t)st->smem, s) != cudaSuccess) {
         cudaGetLastError();
         return FFT_ERR_CUDA;
@@ -550,7 +776,7 @@ fft_status_t ragged_execute(RaggedState* st, const void* in, void* out, void* st
 void ragged_info(const RaggedState* st, fft_plan_info_t* info) {
     info->batch = st->count;
     info->variant = st->variant;
-    info->threads_per_block = kRaggedThreads;
+    info->threads_per_block = ragged_threads(st->variant);
     info->smem_bytes = st->smem;
     info->grid = st->grid;
     info->kernel_kind = 3;
