@@ -199,19 +199,34 @@ def _time_ms(fn, stream, reps: int = 10, warmup: int = 3) -> float:
     return statistics.median(ts)
 
 
-def run_extras(dev, stream, peak):
+EXTRAS = ("adjoint", "ragged", "precision")
+
+
+def run_extras(dev, stream, peak, which=EXTRAS):
     """The other workloads of the hot path, each on its own synthetic data:
     the adjoint (autograd backward), ragged mixed lengths in one graph-captured
     launch, and FP16/BF16 tensor-core radix-16 stages against FP32."""
+    out = {}
+    if "adjoint" in which:
+        out["adjoint"] = extra_adjoint(dev, stream)
+    if "ragged" in which:
+        out["ragged"] = extra_ragged(dev, stream)
+    if "precision" in which:
+        out["precision"] = extra_precision(dev, stream, peak)
+    return out
+
+
+def _gbs(elems, ms):
+    return round(BYTES_PER_ELEM * elems / (ms * 1e-3) / 1e9, 1)
+
+
+def extra_adjoint(dev, stream):
+    """loss = sum |W * FFT(x)|^2, N = 1024, batch = 65536, seed 2: forward and
+    adjoint (unnormalised inverse) kernels and one autograd step."""
     import torch
 
     import paper_2203_09384_gb300 as gb
-    import synth
-    from paper_2203_09384_gb300 import autotune
 
-    out = {}
-    gbs = lambda elems, ms: round(BYTES_PER_ELEM * elems / (ms * 1e-3) / 1e9, 1)  # noqa: E731
-    # -- adjoint: loss = sum |W * FFT(x)|^2, N = 1024, batch = 65536, seed 2
     n, b = 1024, 65536
     g = torch.Generator(device=dev)
     g.manual_seed(2)
@@ -230,13 +245,23 @@ def run_extras(dev, stream, peak):
         loss.backward()
 
     ms_step = _time_ms(step, stream, reps=5)
-    out["adjoint"] = {"workload": "loss=sum|W*FFT(x)|^2, N=1024, batch=65536, x,W ~ CN(0,1), seed 2",
-                      "forward_gbs": gbs(n * b, ms_f), "adjoint_backward_gbs": gbs(n * b, ms_b),
-                      "forward_ms": round(ms_f, 4), "adjoint_ms": round(ms_b, 4),
-                      "autograd_step_ms": round(ms_step, 4),
-                      "note": "step = forward FFT + torch loss ops + adjoint FFT kernel"}
-    del x, w, y, xg
-    # -- ragged: 20000 signals, lengths 2^U{4..11}, seed 3, one launch in a CUDA graph
+    return {"workload": "loss=sum|W*FFT(x)|^2, N=1024, batch=65536, x,W ~ CN(0,1), seed 2",
+            "forward_gbs": _gbs(n * b, ms_f), "adjoint_backward_gbs": _gbs(n * b, ms_b),
+            "forward_ms": round(ms_f, 4), "adjoint_ms": round(ms_b, 4),
+            "autograd_step_ms": round(ms_step, 4),
+            "note": "step = forward FFT + torch loss ops + adjoint FFT kernel"}
+
+
+def extra_ragged(dev, stream):
+    """20000 signals, lengths 2^U{4..11}, seed 3: one ragged launch replayed
+    from a CUDA graph, against one plain launch per length (also a graph) on
+    the same signals and a uniform N = 2048 call of the same element count."""
+    import torch
+
+    import paper_2203_09384_gb300 as gb
+    import synth
+    from paper_2203_09384_gb300 import autotune
+
     lengths = synth.ragged_lengths(20000, seed=3)
     offs = synth.ragged_offsets(lengths)
     xr = synth.ragged_uniform(lengths, seed=3).to(dev)
@@ -251,6 +276,9 @@ def run_extras(dev, stream, peak):
         grouped.append((L, cnt, pos))
         pos += L * cnt
     plans = [(gb.Plan(L, cnt, device=dev), p0, L * cnt) for L, cnt, p0 in grouped]
+    nu = 2048
+    bu = total // nu
+    uni = gb.Plan(nu, bu, device=dev)
     # 163 MB of traffic would sit in the 129 MB L2 after one replay: rotate
     # through 8 buffer pairs (1.3 GB) so every replay reads and writes HBM
     rot = 8
@@ -270,6 +298,7 @@ def run_extras(dev, stream, peak):
     rg = [capture(lambda a=a, o=o: rp.execute(a, o)) for a, o in bufs]
     pg = [capture(lambda a=a, o=o: [p.execute(a[p0:p0 + m], o[p0:p0 + m]) for p, p0, m in plans])
           for a, o in bufs]
+    ug = [capture(lambda a=a, o=o: uni.execute(a[:bu * nu], o[:bu * nu])) for a, o in bufs]
     state = {"i": 0}
 
     def replay(graphs):
@@ -278,15 +307,25 @@ def run_extras(dev, stream, peak):
 
     ms_r = _time_ms(lambda: replay(rg), stream, reps=40, warmup=rot)
     ms_p = _time_ms(lambda: replay(pg), stream, reps=40, warmup=rot)
-    out["ragged"] = {"workload": "20000 C2C FFTs, lengths 2^U{4..11} (seed 3), packed, U[-1,1]",
-                     "elements": total, "variant": tuned["best"], "tuner_ms": tuned["ms"],
-                     "ragged_graph_ms": round(ms_r, 4), "ragged_gbs": gbs(total, ms_r),
-                     "plain_per_length_graph_ms": round(ms_p, 4), "plain_per_length_gbs": gbs(total, ms_p),
-                     "l2": "8 rotating buffer pairs (1.3 GB) so replays are not served from L2",
-                     "launches": {"ragged": 1, "plain": len(plans)}}
-    del rg, pg, bufs
-    del xr, yr
-    # -- precision: FP16/BF16 tensor-core radix-16 vs FP32, N in {256, 2048}, batch 2^17, seed 4
+    ms_u = _time_ms(lambda: replay(ug), stream, reps=40, warmup=rot)
+    return {"workload": "20000 C2C FFTs, lengths 2^U{4..11} (seed 3), packed, U[-1,1]",
+            "elements": total, "variant": tuned["best"], "tuner_ms": tuned["ms"],
+            "ragged_graph_ms": round(ms_r, 4), "ragged_gbs": _gbs(total, ms_r),
+            "plain_per_length_graph_ms": round(ms_p, 4), "plain_per_length_gbs": _gbs(total, ms_p),
+            "uniform_same_size_graph_ms": round(ms_u, 4), "uniform_same_size_gbs": _gbs(bu * nu, ms_u),
+            "uniform_same_size": f"N={nu} x {bu} (one plain launch)",
+            "l2": "8 rotating buffer pairs (1.3 GB) so replays are not served from L2",
+            "launches": {"ragged": 1, "plain": len(plans), "uniform": 1}}
+
+
+def extra_precision(dev, stream, peak):
+    """FP16/BF16 tensor-core radix-16 stages and complex32 storage against FP32,
+    N in {256, 2048}, batch 2^17, signals scaled by 10^U(-3,3), seed 4."""
+    import torch
+
+    import paper_2203_09384_gb300 as gb
+    import synth
+
     prec = {}
     for n in (256, 2048):
         b = 2 ** 17
@@ -300,7 +339,7 @@ def run_extras(dev, stream, peak):
             if dt == "c64":
                 ref.copy_(o)
             d = torch.linalg.vector_norm(o - ref, dim=1) / torch.linalg.vector_norm(ref, dim=1)
-            res[dt] = {"gbs": gbs(n * b, ms), "frac": round(gbs(n * b, ms) / peak, 4), "ms": round(ms, 4),
+            res[dt] = {"gbs": _gbs(n * b, ms), "frac": round(_gbs(n * b, ms) / peak, 4), "ms": round(ms, 4),
                        "gelem_s": round(n * b / ms / 1e6, 2),
                        "max_rel_l2_vs_fp32_path": float(d.max()), "tc_stages": tc_stage_count(p.info())}
         # complex32 storage: 4 B per element each way plus one exponent byte per signal
@@ -316,13 +355,12 @@ def run_extras(dev, stream, peak):
                       "speedup_vs_c64": round(res["c64"]["ms"] / ms, 3),
                       "max_rel_l2_vs_fp32_path": float(d.max()), "tc_stages": 0}
         prec[str(n)] = res
-    out["precision"] = {"workload": "CN(0,1) x 10^U(-3,3) per signal (seed 4), batch 2^17",
-                        "note": "error against the FP64 oracle is in the test suite (bound 5e-3 tensor "
-                                "core, 2^-11 + 1e-5 complex32 storage); here: difference from the FP32 "
-                                "path on the same GPU; c32 input is the complex64 input rounded to "
-                                "complex32 storage, its gbs counts 4+4 B per element + 2 B per signal",
-                        "by_n": prec}
-    return out
+    return {"workload": "CN(0,1) x 10^U(-3,3) per signal (seed 4), batch 2^17",
+            "note": "error against the FP64 oracle is in the test suite (bound 5e-3 tensor "
+                    "core, 2^-11 + 1e-5 complex32 storage); here: difference from the FP32 "
+                    "path on the same GPU; c32 input is the complex64 input rounded to "
+                    "complex32 storage, its gbs counts 4+4 B per element + 2 B per signal",
+            "by_n": prec}
 
 
 def encode_c32(x: torch.Tensor):
@@ -540,8 +578,9 @@ def run_ours(args):
         "gpu_launches": args.steps * len(LOG2NS),
         "clocks": clocks,
     }
-    if not args.no_extras:
-        line["extra"] = run_extras(dev, stream, peak)
+    extras = [] if args.no_extras else [e for e in args.extras.split(",") if e]
+    if extras:
+        line["extra"] = run_extras(dev, stream, peak, extras)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line))
@@ -595,6 +634,8 @@ def main(argv=None):
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the adjoint / ragged / tensor-core workloads")
+    ap.add_argument("--extras", default=",".join(EXTRAS),
+                    help="comma list of the extra workloads to run (adjoint, ragged, precision)")
     ap.add_argument("--only-n", default="", help="comma list of lengths (profiling runs)")
     ap.add_argument("--elems", type=int, default=0, help="elements per length (profiling runs)")
     ap.add_argument("--dtype", default="c64", choices=["c64", "tc_f16", "tc_bf16", "c32"],
@@ -603,6 +644,9 @@ def main(argv=None):
                     help="write profiles/traffic.json from an ncu DRAM-bytes CSV of one sweep step "
                          "(captured with --elems, if given) and exit")
     args = ap.parse_args(argv)
+    bad = [e for e in args.extras.split(",") if e and e not in EXTRAS]
+    if bad:
+        ap.error(f"unknown extras: {bad}")
     if args.write_traffic:
         write_traffic(args.write_traffic, args.elems or ELEMS)
         return 0

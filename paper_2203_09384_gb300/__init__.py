@@ -178,7 +178,8 @@ class RaggedPlan:
         return out
 
     def capture(self, x: torch.Tensor, out: torch.Tensor) -> "torch.cuda.CUDAGraph":
-        """Capture execute(x, out) (counter reset + persistent kernel) in a CUDA graph."""
+        """Capture execute(x, out) in a CUDA graph (the persistent kernel, after a
+        work-counter reset for the variants that use a counter)."""
         s = torch.cuda.Stream(device=x.device)
         s.wait_stream(torch.cuda.current_stream(x.device))
         with torch.cuda.stream(s):
