@@ -68,6 +68,37 @@ def test_ragged_workload_in_a_cuda_graph(workload, variant):
     plan.close()
 
 
+def _per_signal_rel_l2(got: np.ndarray, want: np.ndarray, offsets) -> np.ndarray:
+    starts = np.asarray(offsets[:-1])
+    num = np.add.reduceat(np.abs(got - want) ** 2, starts)
+    den = np.add.reduceat(np.abs(want) ** 2, starts)
+    return np.sqrt(num / np.maximum(den, 1e-300))
+
+
+@pytest.mark.parametrize("variant", list(range(gb.fft_ragged_variant_count())))
+def test_many_replays_two_inputs(workload, variant):
+    """Two graphs of one plan (different buffers) replayed alternately 24
+    times: a race between work items, warp groups or ring slots that a single
+    replay does not expose shows up as a wrong result here."""
+    offsets, x, want = workload
+    xa = x.cuda()
+    xb = xa * (0.5 + 0.25j)  # the transform is linear: expected = want * (0.5 + 0.25j)
+    oa = torch.full_like(xa, float("nan"))
+    ob = torch.full_like(xb, float("nan"))
+    plan = gb.RaggedPlan(offsets, variant=variant)
+    ga = plan.capture(xa, oa)
+    gb_ = plan.capture(xb, ob)
+    for _ in range(12):
+        ga.replay()
+        gb_.replay()
+    torch.cuda.synchronize()
+    assert _abi.lib().fft_plan_get_error(plan.handle) == 0
+    ea = _per_signal_rel_l2(oa.cpu().numpy().astype(np.complex128), want, offsets)
+    eb = _per_signal_rel_l2(ob.cpu().numpy().astype(np.complex128), want * (0.5 + 0.25j), offsets)
+    assert ea.max() <= FP32_TOL and eb.max() <= FP32_TOL, (variant, ea.max(), eb.max())
+    plan.close()
+
+
 def test_every_length_mixed_inverse_inplace():
     rng = np.random.default_rng(17)
     lengths = rng.choice([2 ** k for k in range(1, 12)], size=1500)
