@@ -183,7 +183,11 @@ def tc_stage_count(info) -> int:
     return sum(1 for s in range(info.num_stages) if info.radix[s] == 16)
 
 
-def _time_ms(fn, stream, reps: int = 10, warmup: int = 3) -> float:
+def _time_ms(fn, stream, reps: int = 10, warmup: int = 3, inner: int = 1) -> float:
+    """Median over `reps` samples of the CUDA-event time per call; each sample
+    times `inner` calls enqueued back to back (inner = 1: one call's latency,
+    including the gap while the host enqueues it; inner > 1: the device's
+    throughput for repeated calls, as in the sweep)."""
     import torch
     for _ in range(warmup):
         fn()
@@ -192,10 +196,11 @@ def _time_ms(fn, stream, reps: int = 10, warmup: int = 3) -> float:
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        fn()
+        for _ in range(inner):
+            fn()
         b.record(stream)
         b.synchronize()
-        ts.append(a.elapsed_time(b))
+        ts.append(a.elapsed_time(b) / inner)
     return statistics.median(ts)
 
 
@@ -235,8 +240,8 @@ def extra_adjoint(dev, stream):
     fwd = gb.Plan(n, b, device=dev)
     adj = gb.Plan(n, b, inverse=True, normalized=False, device=dev)
     y = torch.empty_like(x)
-    ms_f = _time_ms(lambda: fwd.execute(x, y), stream)
-    ms_b = _time_ms(lambda: adj.execute(y, x), stream)
+    ms_f = _time_ms(lambda: fwd.execute(x, y), stream, inner=10)
+    ms_b = _time_ms(lambda: adj.execute(y, x), stream, inner=10)
     xg = x.clone().requires_grad_(True)
 
     def step():
@@ -249,6 +254,7 @@ def extra_adjoint(dev, stream):
             "forward_gbs": _gbs(n * b, ms_f), "adjoint_backward_gbs": _gbs(n * b, ms_b),
             "forward_ms": round(ms_f, 4), "adjoint_ms": round(ms_b, 4),
             "autograd_step_ms": round(ms_step, 4),
+            "timing": "kernels: 10 calls back to back per sample, median of 10 samples",
             "note": "step = forward FFT + torch loss ops + adjoint FFT kernel"}
 
 
@@ -308,12 +314,21 @@ def extra_ragged(dev, stream):
     ms_r = _time_ms(lambda: replay(rg), stream, reps=40, warmup=rot)
     ms_p = _time_ms(lambda: replay(pg), stream, reps=40, warmup=rot)
     ms_u = _time_ms(lambda: replay(ug), stream, reps=40, warmup=rot)
+    # device throughput: the 8 graphs replayed back to back per sample
+    bt_r = _time_ms(lambda: replay(rg), stream, reps=10, warmup=rot, inner=rot)
+    bt_p = _time_ms(lambda: replay(pg), stream, reps=10, warmup=rot, inner=rot)
+    bt_u = _time_ms(lambda: replay(ug), stream, reps=10, warmup=rot, inner=rot)
     return {"workload": "20000 C2C FFTs, lengths 2^U{4..11} (seed 3), packed, U[-1,1]",
             "elements": total, "variant": tuned["best"], "tuner_ms": tuned["ms"],
             "ragged_graph_ms": round(ms_r, 4), "ragged_gbs": _gbs(total, ms_r),
             "plain_per_length_graph_ms": round(ms_p, 4), "plain_per_length_gbs": _gbs(total, ms_p),
             "uniform_same_size_graph_ms": round(ms_u, 4), "uniform_same_size_gbs": _gbs(bu * nu, ms_u),
             "uniform_same_size": f"N={nu} x {bu} (one plain launch)",
+            "back_to_back": {"ragged_ms": round(bt_r, 4), "ragged_gbs": _gbs(total, bt_r),
+                             "plain_per_length_ms": round(bt_p, 4), "plain_per_length_gbs": _gbs(total, bt_p),
+                             "uniform_same_size_ms": round(bt_u, 4), "uniform_same_size_gbs": _gbs(bu * nu, bt_u)},
+            "timing": "*_graph_ms: one graph replay per CUDA-event sample (latency, with the host's enqueue gap); "
+                      "back_to_back: 8 replays per sample (device throughput)",
             "l2": "8 rotating buffer pairs (1.3 GB) so replays are not served from L2",
             "launches": {"ragged": 1, "plain": len(plans), "uniform": 1}}
 
@@ -335,7 +350,7 @@ def extra_precision(dev, stream, peak):
         for dt in ("c64", "tc_f16", "tc_bf16"):
             p = gb.Plan(n, b, dtype=dt, device=dev)
             o = torch.empty_like(xs)
-            ms = _time_ms(lambda: p.execute(xs, o), stream)
+            ms = _time_ms(lambda: p.execute(xs, o), stream, inner=10)
             if dt == "c64":
                 ref.copy_(o)
             d = torch.linalg.vector_norm(o - ref, dim=1) / torch.linalg.vector_norm(ref, dim=1)
@@ -346,7 +361,7 @@ def extra_precision(dev, stream, peak):
         hs, he = encode_c32(xs)
         p = gb.Plan(n, b, dtype="c32", device=dev)
         ho, hoe = torch.empty_like(hs), torch.empty_like(he)
-        ms = _time_ms(lambda: p.execute_c32(hs, he, ho, hoe), stream)
+        ms = _time_ms(lambda: p.execute_c32(hs, he, ho, hoe), stream, inner=10)
         o = decode_c32(ho, hoe)
         d = torch.linalg.vector_norm(o - ref, dim=1) / torch.linalg.vector_norm(ref, dim=1)
         nbytes = 8 * n * b + 2 * b
@@ -356,6 +371,7 @@ def extra_precision(dev, stream, peak):
                       "max_rel_l2_vs_fp32_path": float(d.max()), "tc_stages": 0}
         prec[str(n)] = res
     return {"workload": "CN(0,1) x 10^U(-3,3) per signal (seed 4), batch 2^17",
+            "timing": "10 calls back to back per CUDA-event sample, median of 10 samples",
             "note": "error against the FP64 oracle is in the test suite (bound 5e-3 tensor "
                     "core, 2^-11 + 1e-5 complex32 storage); here: difference from the FP32 "
                     "path on the same GPU; c32 input is the complex64 input rounded to "
