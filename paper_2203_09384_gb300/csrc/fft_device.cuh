@@ -429,10 +429,10 @@ struct Cfg {
 // layout without swizzle: 8-row x 16-byte core matrices, 128 B apart along K
 // (leading byte offset) and 512 B apart along M/N (stride byte offset).
 //
-// Dynamic range: each butterfly row is scaled by its own power of two before
-// the FP16 / BF16 conversion (see tc_dft16), which gives every row at least
-// the precision a per-signal power-of-two scale gives the signal's largest
-// row, with no exchange between threads.
+// Dynamic range: for FP16 each butterfly row is scaled by its own power of two
+// before the conversion (see tc_dft16), which gives every row at least the
+// precision a per-signal power-of-two scale gives the signal's largest row,
+// with no exchange between threads; BF16 needs no scale.
 // ---------------------------------------------------------------------------
 struct TcCtx {
     uint32_t tmem = 0;   // TMEM base address of the accumulators
@@ -561,21 +561,29 @@ __device__ __forceinline__ int pow2_exponent(float mx) {
 }
 
 // Every thread of the block calls this with its own butterfly's 16 inputs.
-// The 16-point DFT is linear, so each row is scaled by its own power of two
-// 2^-e (exact) before the FP16/BF16 conversion, which keeps every operand in
+// FP16: the 16-point DFT is linear, so each row is scaled by its own power of
+// two 2^-e (exact) before the conversion, which keeps every operand in
 // [-1, 1) whatever the signal's magnitude, and the FP32 accumulators are
-// multiplied by 2^e after the read-back.
+// multiplied by 2^e after the read-back.  BF16 has FP32's exponent range, and
+// a power-of-two scale commutes with BF16 rounding and with the FP32
+// accumulation (normal range), so for BF16 the scale would change no result
+// and is left out.
 template <class C>
 __device__ __forceinline__ void tc_dft16(float2* v, TcCtx& tc) {
+    constexpr bool kScaled = C::TC == 1;  // FP16 operands
     const int tid = threadIdx.x;
     const int row = tid & 127;
-    float mx = 0.0f;
+    float up = 1.0f;
+    if constexpr (kScaled) {
+        float mx = 0.0f;
 #pragma unroll
-    for (int i = 0; i < 16; ++i) mx = fmaxf(mx, fmaxf(fabsf(v[i].x), fabsf(v[i].y)));
-    const int e = pow2_exponent(mx);
-    const float down = exp2i(-e), up = exp2i(e);
+        for (int i = 0; i < 16; ++i) mx = fmaxf(mx, fmaxf(fabsf(v[i].x), fabsf(v[i].y)));
+        const int e = pow2_exponent(mx);
+        const float down = exp2i(-e);
+        up = exp2i(e);
 #pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = make_float2(v[i].x * down, v[i].y * down);
+        for (int i = 0; i < 16; ++i) v[i] = make_float2(v[i].x * down, v[i].y * down);
+    }
     // XB = -2 writes A over the slot the inputs were just gathered from:
     // every thread must be done reading it
     if constexpr (C::kAInRing) __syncthreads();
@@ -642,7 +650,10 @@ __device__ __forceinline__ void tc_dft16(float2* v, TcCtx& tc) {
         : "r"(taddr));
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-    for (int q = 0; q < 16; ++q) v[q] = make_float2(__uint_as_float(r[q]) * up, __uint_as_float(r[16 + q]) * up);
+    for (int q = 0; q < 16; ++q) {
+        v[q] = make_float2(__uint_as_float(r[q]), __uint_as_float(r[16 + q]));
+        if constexpr (kScaled) v[q] = make_float2(v[q].x * up, v[q].y * up);
+    }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
 }
 

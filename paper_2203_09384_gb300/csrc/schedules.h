@@ -13,7 +13,8 @@
 //             (TMA) prefetch, D-1 tiles ahead of the one being transformed,
 //      TC = 0: FP32 butterflies; 1 / 2: every radix-16 stage runs as a dense
 //           16 x 16 complex product on FP16 / BF16 tensor cores (tcgen05),
-//           FP32 accumulation, per-signal power-of-two prescale,
+//           FP32 accumulation (FP16: a power-of-two prescale per butterfly
+//           row; BF16 shares FP32's exponent range and needs none),
 //      XB = exchange buffers: 0 = automatic, 1 = one buffer and two barriers
 //           per exchange (less shared memory, more resident blocks),
 //           -1 = none: with PIPE >= 2, every exchange reuses the ring slot

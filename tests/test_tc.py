@@ -2,7 +2,8 @@
 
 Workload: complex N(0,1) signals, each scaled by 10^u with u ~ U(-3, 3)
 (seed 4), so that a fixed FP16 range would overflow or underflow without the
-per-signal power-of-two prescale.  Bar: per-signal relative L2 <= 5e-3.
+power-of-two prescale of the FP16 path (BF16 shares FP32's exponent range).
+Bar: per-signal relative L2 <= 5e-3.
 """
 import numpy as np
 import pytest
@@ -59,7 +60,8 @@ def test_precision_workload_sample(n, dtype):
 @pytest.mark.parametrize("dtype", ["tc_f16", "tc_bf16"])
 def test_tc_exact_cases(dtype):
     """Inputs whose products are exact in FP16/BF16: delta -> all ones; the
-    prescale is a power of two, so huge and tiny deltas come out exact too."""
+    FP16 prescale is a power of two and BF16 shares FP32's range, so huge and
+    tiny deltas come out exact too."""
     for n in TC_LENGTHS:
         for amp in (1.0, 2.0 ** 40, 2.0 ** -40):
             d = synth.delta(n, 0, batch=3) * amp
