@@ -974,7 +974,7 @@ __device__ __forceinline__ void rest_stages_in_ring(float2 (&v)[C::E], float2* b
 template <class C, bool INV>
 __global__ void __launch_bounds__(C::NT, C::MINB)
     fft_stockham_slot_ring_kernel(const float2* in, float2* out, int64_t batch, const float2* __restrict__ tw,
-                                     float scale, int* err, uint64_t wait_ns, int stall) {
+                                  float scale, int* err, uint64_t wait_ns, int stall) {
     static_assert(C::kInRing, "in-ring schedules only");
     constexpr int D = C::PIPE;
     constexpr int TILE = C::S * C::N;
