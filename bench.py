@@ -67,10 +67,10 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(log2n: int):
+def ncu_traffic(log2n: int, path: str | None = None):
     """DRAM bytes per launch from the committed ncu summary, or None when the
     kernel sources changed since it was captured."""
-    p = os.path.join(ROOT, "profiles", "traffic.json")
+    p = path or os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
     with open(p) as f:
@@ -121,9 +121,15 @@ class ClockSampler:
             self.proc.kill()
         if self.thread:
             self.thread.join(timeout=2)
+        return self.summarize(self.lines)
+
+    @staticmethod
+    def summarize(lines):
+        """Median SM clock, max clock, throttle reasons seen Active, sample
+        count and peak power from nvidia-smi CSV lines (FIELDS order)."""
         sm, smax, power, reasons = [], None, [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in self.lines:
+        for line in lines:
             parts = [p.strip() for p in line.split(",")]
             if len(parts) < 9:
                 continue
@@ -605,7 +611,7 @@ def run_ours(args):
     return 0
 
 
-def write_traffic(csv_path: str, elems: int) -> None:
+def write_traffic(csv_path: str, elems: int, out_path: str | None = None) -> dict:
     """Write profiles/traffic.json from an ncu CSV log of one forward launch per
     length in sweep order (dram__bytes_read.sum and dram__bytes_write.sum),
     scaled to the benchmark's 2^28 elements per launch when captured smaller,
@@ -634,10 +640,11 @@ def write_traffic(csv_path: str, elems: int) -> None:
            "note": "dram__bytes_read.sum + dram__bytes_write.sum of one forward launch per length"
                    + (f", times {factor:g} (traffic grows in proportion to the elements)" if factor != 1 else ""),
            "bytes_per_launch": {str(2 ** k): per_id[i] * factor for k, i in zip(LOG2NS, order)}}
-    with open(os.path.join(ROOT, "profiles", "traffic.json"), "w") as f:
+    with open(out_path or os.path.join(ROOT, "profiles", "traffic.json"), "w") as f:
         json.dump(out, f, indent=1)
         f.write("\n")
     print(json.dumps(out["bytes_per_launch"]))
+    return out
 
 
 def main(argv=None):
