@@ -281,6 +281,32 @@ def test_full_size_sampled(n):
     torch.cuda.empty_cache()
 
 
+@pytest.mark.parametrize("n", [16, 2048])
+def test_beyond_2_32_elements(n):
+    """One call over more than 2^32 complex64 elements (34 GB in, 34 GB out):
+    64-bit signal and element indexing in every kernel of the length; the
+    signals on both sides of element 2^32 and the last ones are checked."""
+    batch = (2 ** 32) // n + 3
+    if torch.cuda.mem_get_info()[0] < 2 * 8 * n * batch + (4 << 30):
+        pytest.skip("needs about 70 GB of free device memory")
+    x = torch.empty(batch, n, dtype=torch.complex64, device="cuda")
+    torch.view_as_real(x).uniform_(-1.0, 1.0, generator=torch.Generator(device="cuda").manual_seed(7))
+    out = torch.empty_like(x)
+    plan = gb.Plan(n, batch)
+    plan.execute(x, out)
+    torch.cuda.synchronize()
+    assert plan.error() == 0
+    plan.close()
+    first_hi = (2 ** 32) // n  # first signal at or past element 2^32
+    idx = np.unique(np.concatenate([[0], np.arange(first_hi - 3, batch)]))
+    ti = torch.from_numpy(idx).cuda()
+    xs = x.index_select(0, ti).cpu()
+    ys = to_np(out.index_select(0, ti))
+    del x, out
+    torch.cuda.empty_cache()
+    assert max_rel_l2(ys, oracle_of(xs)) <= FP32_TOL
+
+
 @pytest.mark.parametrize("n,batch", [(2, 70001), (64, 3 * 2 ** 20 // 64 + 5), (2048, 9001), (256, 1)])
 def test_execute_host_pipeline(n, batch):
     """fft_execute_host: pinned host buffers, chunked copy / transform / copy
