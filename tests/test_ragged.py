@@ -99,6 +99,31 @@ def test_many_replays_two_inputs(workload, variant):
     plan.close()
 
 
+def test_offsets_beyond_2_32_elements():
+    """Signals of every length placed on both sides of element 2^32 of one
+    34 GB buffer (64-bit offsets), transformed in place by every variant."""
+    lengths = np.array([2 ** k for k in range(1, 12)] * 3)
+    start = 2 ** 32 - 2 * 2048  # even; the signals straddle element 2^32
+    offsets = np.concatenate([[start], start + np.cumsum(lengths)])
+    total = int(offsets[-1])
+    if torch.cuda.mem_get_info()[0] < 8 * total + (4 << 30):
+        pytest.skip("needs about 40 GB of free device memory")
+    seg = synth.uniform(1, total - start, seed=23).reshape(-1)
+    want = oracle_ragged(seg.numpy(), offsets - start)
+    buf = torch.empty(total, dtype=torch.complex64, device="cuda")
+    for variant in range(gb.fft_ragged_variant_count()):
+        buf[start:].copy_(seg)
+        plan = gb.RaggedPlan(offsets, variant=variant)
+        plan.execute(buf, buf)
+        torch.cuda.synchronize()
+        assert _abi.lib().fft_plan_get_error(plan.handle) == 0
+        plan.close()
+        got = buf[start:].cpu().numpy().astype(np.complex128)
+        assert per_signal_max_err(got, want, offsets - start) <= FP32_TOL, variant
+    del buf
+    torch.cuda.empty_cache()
+
+
 def test_every_length_mixed_inverse_inplace():
     rng = np.random.default_rng(17)
     lengths = rng.choice([2 ** k for k in range(1, 12)], size=1500)
