@@ -238,9 +238,12 @@ GBFFT_API int fft_variant_dtype(int64_t n, int variant);
 
 /*
  * Wall-time limit for the device-side waits of this plan's kernels (the
- * bulk-copy prefetch ring waits on mbarriers).  A wait that runs out records
- * FFT_ERR_TIMEOUT in the plan's error word (see fft_plan_get_error), stops
- * waiting and lets the kernel finish.  Default 4 s.  0 is rejected.
+ * bulk-copy prefetch rings and the tensor-core MMA completion wait on
+ * mbarriers).  A wait that runs out records FFT_ERR_TIMEOUT in the plan's
+ * error word (see fft_plan_get_error); the block then stops waiting and
+ * issuing, skips its stores and finishes, after waiting once more (with the
+ * same limit) for copies or MMAs it had already issued.  Default 4 s.  0 is
+ * rejected.
  */
 GBFFT_API fft_status_t fft_plan_set_wait_limit(fft_plan_t plan, uint64_t nanoseconds);
 
