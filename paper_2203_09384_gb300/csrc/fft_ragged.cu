@@ -523,8 +523,9 @@ namespace {
 
 template <int V0>
 struct RaggedHost {
-    static constexpr int V = V0 & 1;  // schedule set
+    // V0 & 1 is the schedule set; variants 2 and 3 use only kernel()
     static int signals_per_tile(int L) {
+        constexpr int V = V0 & 1;
         switch (L) {
 #define GBFFT_RS(L) \
     case L: return RCfg<V, L>::type::S;
@@ -536,6 +537,7 @@ struct RaggedHost {
     }
     // twiddle table of length 2^L's schedule (same layout as the uniform path)
     static int twiddles(int L) {
+        constexpr int V = V0 & 1;
         switch (L) {
 #define GBFFT_RT(L) \
     case L: return RCfg<V, L>::type::kTwiddles;
@@ -557,6 +559,7 @@ struct RaggedHost {
         }
     }
     static void fill_twiddles(int L, float* host) {
+        constexpr int V = V0 & 1;
         switch (L) {
 #define GBFFT_RF(L) \
     case L: fill<typename RCfg<V, L>::type>(host); break;
