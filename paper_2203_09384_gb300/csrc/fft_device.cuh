@@ -370,6 +370,9 @@ struct Cfg {
     // memory, more resident blocks.
     static constexpr bool kInRing = XB_ < 0;
     static constexpr bool kAInRing = XB_ == -2;
+    // XB = -3: exchanges in the ring slot and the tensor-core A operand in
+    // TMEM (written with tcgen05.st, 16 columns after the accumulators)
+    static constexpr bool kAInTmem = XB_ == -3;
     // exchange buffers: one suffices when a signal stays in one warp; across
     // warps two let one barrier per exchange do (XB = 1 forces one buffer and
     // a second barrier, halving the shared memory of the exchange)
@@ -379,11 +382,14 @@ struct Cfg {
     // 0: FP32 butterflies; 1 / 2: radix-16 stages on FP16 / BF16 tensor cores
     static constexpr int TC = TC_;
     static constexpr int kTcTiles = NT / 128;  // 128-row MMA tiles per radix-16 stage
-    static constexpr int kTcCols = 32 * kTcTiles;  // TMEM columns (FP32 accumulators)
+    // TMEM columns: FP32 accumulators (32 per tile), plus 16 for an A operand
+    // kept in TMEM, rounded up to the allocation granularity
+    static constexpr int kTcCols = kAInTmem ? 64 : 32 * kTcTiles;
+    static constexpr int kTcACol = 32 * kTcTiles;  // first A column (kAInTmem)
     static constexpr int kTcOffset = (((kSmemElems + kRingElems) * 8 + 8 * PIPE) + 127) / 128 * 128;
     // A operand (kTcTiles x 8 KiB, unless it lives in the ring slot), B (2 KiB),
     // the MMA-completion mbarrier and the TMEM address slot
-    static constexpr int kTcABytes = kAInRing ? 0 : kTcTiles * 8192;
+    static constexpr int kTcABytes = (kAInRing || kAInTmem) ? 0 : kTcTiles * 8192;
     static constexpr int kTcBytes = TC ? kTcABytes + 2048 + 128 : 0;
     static constexpr int kSmemBytes = TC ? kTcOffset + kTcBytes : (kSmemElems + kRingElems) * 8 + 8 * PIPE;
     __host__ __device__ static constexpr int radix(int s) {
@@ -411,6 +417,7 @@ struct Cfg {
     static_assert(PIPE == 0 || PIPE >= 2, "the bulk-copy ring needs at least two slots");
     static_assert(!kInRing || PIPE >= 2, "exchanges in the ring slot need the bulk-copy ring");
     static_assert(!kAInRing || TC == 0 || kTcTiles * 8192 <= S * N * 8, "the A operand must fit in a ring slot");
+    static_assert(!kAInTmem || TC == 0 || kTcTiles == 1, "A in TMEM: one 128-row tile per block");
     static_assert(TC == 0 || (E == 16 && NT % 128 == 0 && (kTcCols == 32 || kTcCols == 64 || kTcCols == 128)),
                   "tensor-core radix-16 stages need one 16-point butterfly per thread and 128-row tiles");
 };
@@ -587,43 +594,75 @@ __device__ __forceinline__ void tc_dft16(float2* v, TcCtx& tc) {
     // XB = -2 writes A over the slot the inputs were just gathered from:
     // every thread must be done reading it
     if constexpr (C::kAInRing) __syncthreads();
-    unsigned char* arow = tc.a + (tid >> 7) * 8192 + (row >> 3) * 512 + (row & 7) * 16;
+    if constexpr (C::kAInTmem) {
+        // row `row` of A in TMEM lane `row`: 16 columns of two 16-bit K values
+        // each, K order Re x_0..15, Im x_0..15 (as in the shared-memory layout)
+        uint32_t q[16];
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {  // K chunk c: Re x_0..7, Re x_8..15, Im x_0..7, Im x_8..15
-        const int o = (c & 1) * 8;
-        uint4 q;
-        if (c < 2) {
-            q.x = pack2<C::TC>(v[o + 0].x, v[o + 1].x);
-            q.y = pack2<C::TC>(v[o + 2].x, v[o + 3].x);
-            q.z = pack2<C::TC>(v[o + 4].x, v[o + 5].x);
-            q.w = pack2<C::TC>(v[o + 6].x, v[o + 7].x);
-        } else {
-            q.x = pack2<C::TC>(v[o + 0].y, v[o + 1].y);
-            q.y = pack2<C::TC>(v[o + 2].y, v[o + 3].y);
-            q.z = pack2<C::TC>(v[o + 4].y, v[o + 5].y);
-            q.w = pack2<C::TC>(v[o + 6].y, v[o + 7].y);
+        for (int i = 0; i < 8; ++i) {
+            q[i] = pack2<C::TC>(v[2 * i].x, v[2 * i + 1].x);
+            q[8 + i] = pack2<C::TC>(v[2 * i].y, v[2 * i + 1].y);
         }
-        *reinterpret_cast<uint4*>(arow + c * 128) = q;
+        const uint32_t ta = tc.tmem + ((uint32_t)(((tid >> 5) & 3) * 32) << 16) + C::kTcACol;
+        asm volatile(
+            "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
+                ta),
+            "r"(q[0]), "r"(q[1]), "r"(q[2]), "r"(q[3]), "r"(q[4]), "r"(q[5]), "r"(q[6]), "r"(q[7]), "r"(q[8]),
+            "r"(q[9]), "r"(q[10]), "r"(q[11]), "r"(q[12]), "r"(q[13]), "r"(q[14]), "r"(q[15])
+            : "memory");
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+    } else {
+        unsigned char* arow = tc.a + (tid >> 7) * 8192 + (row >> 3) * 512 + (row & 7) * 16;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {  // K chunk c: Re x_0..7, Re x_8..15, Im x_0..7, Im x_8..15
+            const int o = (c & 1) * 8;
+            uint4 q;
+            if (c < 2) {
+                q.x = pack2<C::TC>(v[o + 0].x, v[o + 1].x);
+                q.y = pack2<C::TC>(v[o + 2].x, v[o + 3].x);
+                q.z = pack2<C::TC>(v[o + 4].x, v[o + 5].x);
+                q.w = pack2<C::TC>(v[o + 6].x, v[o + 7].x);
+            } else {
+                q.x = pack2<C::TC>(v[o + 0].y, v[o + 1].y);
+                q.y = pack2<C::TC>(v[o + 2].y, v[o + 3].y);
+                q.z = pack2<C::TC>(v[o + 4].y, v[o + 5].y);
+                q.w = pack2<C::TC>(v[o + 6].y, v[o + 7].y);
+            }
+            *reinterpret_cast<uint4*>(arow + c * 128) = q;
+        }
+        fence_proxy_async_smem();  // make the rows visible to the tensor core
     }
-    fence_proxy_async_smem();  // make the rows visible to the tensor core
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const bool issuer = tid == 0 && !tc.stall && !tc.dead;
     if (issuer) {
         const uint32_t idesc = umma_idesc<C::TC>();
-        const uint32_t a0 = smem_u32(tc.a), b0 = smem_u32(tc.b);
+        const uint32_t b0 = smem_u32(tc.b);
+        if constexpr (C::kAInTmem) {
 #pragma unroll
-        for (int t = 0; t < C::kTcTiles; ++t) {
-#pragma unroll
-            for (int ks = 0; ks < 2; ++ks) {
-                const uint64_t da = umma_smem_desc(a0 + t * 8192 + ks * 256);
+            for (int ks = 0; ks < 2; ++ks) {  // K = 16 per step: 8 A columns
                 const uint64_t db = umma_smem_desc(b0 + ks * 256);
                 asm volatile(
                     "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tc.tmem + 32 * t),
-                    "l"(da), "l"(db), "r"(idesc), "r"(ks)
+                    "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(tc.tmem),
+                    "r"(tc.tmem + C::kTcACol + 8 * ks), "l"(db), "r"(idesc), "r"(ks)
                     : "memory");
+            }
+        } else {
+            const uint32_t a0 = smem_u32(tc.a);
+#pragma unroll
+            for (int t = 0; t < C::kTcTiles; ++t) {
+#pragma unroll
+                for (int ks = 0; ks < 2; ++ks) {
+                    const uint64_t da = umma_smem_desc(a0 + t * 8192 + ks * 256);
+                    const uint64_t db = umma_smem_desc(b0 + ks * 256);
+                    asm volatile(
+                        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tc.tmem + 32 * t),
+                        "l"(da), "l"(db), "r"(idesc), "r"(ks)
+                        : "memory");
+                }
             }
         }
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(

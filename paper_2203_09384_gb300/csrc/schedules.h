@@ -19,7 +19,7 @@
 //           per exchange (less shared memory, more resident blocks),
 //           -1 = none: with PIPE >= 2, every exchange reuses the ring slot
 //           the tile arrived in; -2 = as -1, and the tensor-core A operand
-//           lives in that slot too,
+//           lives in that slot too; -3 = as -1, with the A operand in TMEM,
 //      CH = cache hints: bit 0 plain loads, bit 1 plain stores (else
 //           evict-first); the defaults are the measured best per length)
 // Threads per block = S * N / E.  Stage 0 with R0 = E/2 (and the last stage,
@@ -51,26 +51,26 @@
     GX(10, 1, 16, 2, 8, 16, 8, 0, 1, 0, 0, 0, 0) \
     GX(10, 2, 16, 2, 8, 16, 8, 0, 4, 0, 0, 0, 0) \
     GX(10, 3, 16, 2, 8, 16, 8, 0, 2, 3, 0, 0, 0) \
-    GX(10, 4, 16, 2, 8, 16, 8, 0, 5, 2, 1, -2, 0) \
-    GX(10, 5, 16, 2, 8, 16, 8, 0, 5, 2, 2, -2, 0) \
+    GX(10, 4, 16, 2, 8, 16, 8, 0, 5, 2, 1, -3, 0) \
+    GX(10, 5, 16, 2, 8, 16, 8, 0, 5, 2, 2, -3, 0) \
     GX(10, 6, 16, 2, 8, 16, 8, 0, 2, 2, 1, 0, 0) \
     GX(10, 7, 16, 2, 8, 16, 8, 0, 2, 2, 2, 0, 0) \
     GX(10, 10, 16, 2, 8, 16, 8, 0, 5, 2, 0, -1, 2) \
-    GX(10, 11, 16, 2, 8, 16, 8, 0, 5, 2, 1, -1, 0) \
-    GX(10, 12, 16, 2, 8, 16, 8, 0, 5, 2, 2, -1, 0) \
+    GX(10, 11, 16, 2, 8, 16, 8, 0, 5, 2, 1, -2, 0) \
+    GX(10, 12, 16, 2, 8, 16, 8, 0, 5, 2, 2, -2, 0) \
     GX(10, 13, 16, 2, 8, 16, 8, 0, 4, 2, 1, 1, 0) \
     GX(10, 14, 16, 2, 8, 16, 8, 0, 4, 2, 2, 1, 0) \
     GX(11, 0, 16, 1, 8, 16, 16, 0, 5, 2, 0, -1, 2) \
     GX(11, 1, 16, 1, 8, 16, 16, 0, 1, 0, 0, 0, 0) \
     GX(11, 2, 16, 1, 8, 16, 16, 0, 2, 3, 0, 0, 0) \
     GX(11, 3, 16, 2, 8, 16, 16, 0, 1, 2, 0, 0, 0) \
-    GX(11, 4, 16, 1, 8, 16, 16, 0, 5, 2, 1, -2, 0) \
-    GX(11, 5, 16, 1, 8, 16, 16, 0, 5, 2, 2, -2, 0) \
+    GX(11, 4, 16, 1, 8, 16, 16, 0, 5, 2, 1, -3, 0) \
+    GX(11, 5, 16, 1, 8, 16, 16, 0, 5, 2, 2, -3, 0) \
     GX(11, 6, 16, 1, 8, 16, 16, 0, 3, 2, 1, 0, 0) \
     GX(11, 7, 16, 1, 8, 16, 16, 0, 3, 2, 2, 0, 0) \
     GX(11, 10, 16, 1, 8, 16, 16, 0, 3, 2, 0, 0, 2) \
-    GX(11, 11, 16, 1, 8, 16, 16, 0, 5, 2, 1, -1, 0) \
-    GX(11, 12, 16, 1, 8, 16, 16, 0, 5, 2, 2, -1, 0) \
+    GX(11, 11, 16, 1, 8, 16, 16, 0, 5, 2, 1, -2, 0) \
+    GX(11, 12, 16, 1, 8, 16, 16, 0, 5, 2, 2, -2, 0) \
     GX(11, 13, 16, 1, 8, 16, 16, 0, 4, 2, 1, 1, 0) \
     GX(11, 14, 16, 1, 8, 16, 16, 0, 4, 2, 2, 1, 0)
 
