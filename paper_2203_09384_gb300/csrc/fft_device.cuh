@@ -386,6 +386,13 @@ struct Cfg {
     // kept in TMEM, rounded up to the allocation granularity
     static constexpr int kTcCols = kAInTmem ? 64 : 32 * kTcTiles;
     static constexpr int kTcACol = 32 * kTcTiles;  // first A column (kAInTmem)
+    // radix-16 stages on the tensor cores
+    static constexpr int kTcStages = TC ? (R0 == 16) + (R1 == 16) + (R2 == 16) + (R3 == 16) : 0;
+    // FP16 dynamic range: a signal spanning warps is scaled once per tile by
+    // its own power of two (measured faster there); a signal within one warp
+    // scales each butterfly row before its conversion.  BF16: no scale.
+    static constexpr bool kTcSignalScale = TC == 1 && T > 32;
+    static constexpr bool kTcRowScale = TC == 1 && T <= 32;
     static constexpr int kTcOffset = (((kSmemElems + kRingElems) * 8 + 8 * PIPE) + 127) / 128 * 128;
     // A operand (kTcTiles x 8 KiB, unless it lives in the ring slot), B (2 KiB),
     // the MMA-completion mbarrier and the TMEM address slot
@@ -418,6 +425,10 @@ struct Cfg {
     static_assert(!kInRing || PIPE >= 2, "exchanges in the ring slot need the bulk-copy ring");
     static_assert(!kAInRing || TC == 0 || kTcTiles * 8192 <= S * N * 8, "the A operand must fit in a ring slot");
     static_assert(!kAInTmem || TC == 0 || kTcTiles == 1, "A in TMEM: one 128-row tile per block");
+    // a signal spanning warps finds its maximum through shared memory after a
+    // block barrier, so its first stage cannot be a tensor-core one
+    static_assert(!kTcSignalScale || (R0 != 16 && PIPE >= 2 && NT <= 256),
+                  "FP16 per-signal scale: signals spanning warps only in ring kernels");
     static_assert(TC == 0 || (E == 16 && NT % 128 == 0 && (kTcCols == 32 || kTcCols == 64 || kTcCols == 128)),
                   "tensor-core radix-16 stages need one 16-point butterfly per thread and 128-row tiles");
 };
@@ -436,10 +447,11 @@ struct Cfg {
 // layout without swizzle: 8-row x 16-byte core matrices, 128 B apart along K
 // (leading byte offset) and 512 B apart along M/N (stride byte offset).
 //
-// Dynamic range: for FP16 each butterfly row is scaled by its own power of two
-// before the conversion (see tc_dft16), which gives every row at least the
-// precision a per-signal power-of-two scale gives the signal's largest row,
-// with no exchange between threads; BF16 needs no scale.
+// Dynamic range: BF16 shares FP32's exponent range and a power-of-two scale
+// commutes with its rounding, so BF16 operands are converted unscaled.  FP16
+// operands are scaled by powers of two: per butterfly row when a signal stays
+// in one warp (see tc_dft16), per signal when it spans warps (tc_norm_begin);
+// both give each row at least the precision a per-signal scale gives it.
 // ---------------------------------------------------------------------------
 struct TcCtx {
     uint32_t tmem = 0;   // TMEM base address of the accumulators
@@ -450,6 +462,8 @@ struct TcCtx {
     int* err = nullptr;
     uint64_t wait_ns = 0;
     int mma_pending = -1;  // thread 0: parity of an MMA phase it gave up waiting for
+    int e = 0;             // FP16: the current tile's signal exponent (data scaled by 2^-e)
+    float* red = nullptr;  // FP16: per-warp signal maxima (signals spanning warps)
     bool dead = false;     // a bounded wait gave up: stop waiting, issue nothing, finish
     bool stall = false;    // failure-detection test mode: issue no MMA
 };
@@ -511,6 +525,7 @@ __device__ __forceinline__ void tc_setup(TcCtx& tc, unsigned char* base, int* er
     tc.b = base + C::kTcABytes;
     tc.bar = reinterpret_cast<uint64_t*>(tc.b + 2048);
     uint32_t* slot = reinterpret_cast<uint32_t*>(tc.b + 2048 + 8);
+    tc.red = reinterpret_cast<float*>(tc.b + 2048 + 16);  // NT / 32 <= 8 floats
     tc.err = err;
     tc.wait_ns = wait_ns;
     if ((threadIdx.x >> 5) == 0) {
@@ -531,6 +546,7 @@ __device__ __forceinline__ void tc_setup(TcCtx& tc, unsigned char* base, int* er
         float val;
         if (n < 16) val = k < 16 ? w.x : w.y;  // Re y: c, s
         else val = k < 16 ? -w.y : w.x;        // Im y: -s, c
+        if (C::kTcSignalScale) val *= 0.0625f;  // F / 16 (exact): no stage grows the data
         *reinterpret_cast<uint16_t*>(tc.b + (n >> 3) * 512 + (k >> 3) * 128 + (n & 7) * 16 + (k & 7) * 2) =
             to_bits<C::TC>(val);
     }
@@ -567,21 +583,19 @@ __device__ __forceinline__ int pow2_exponent(float mx) {
     return e < -120 ? -120 : (e > 126 ? 126 : e);
 }
 
-// Every thread of the block calls this with its own butterfly's 16 inputs.
-// FP16: the 16-point DFT is linear, so each row is scaled by its own power of
-// two 2^-e (exact) before the conversion, which keeps every operand in
-// [-1, 1) whatever the signal's magnitude, and the FP32 accumulators are
-// multiplied by 2^e after the read-back.  BF16 has FP32's exponent range, and
-// a power-of-two scale commutes with BF16 rounding and with the FP32
-// accumulation (normal range), so for BF16 the scale would change no result
-// and is left out.
+// Every thread of the block calls this with its own butterfly's 16 inputs
+// and gets back F x, or F x / 16 when the signal was scaled as a whole
+// (kTcSignalScale: B holds F / 16, see tc_norm_begin).  With kTcRowScale the
+// row is scaled here by its own power of two 2^-e (exact) before the FP16
+// conversion, which keeps every operand in [-1, 1) whatever the signal's
+// magnitude, and the FP32 accumulators are multiplied by 2^e after the
+// read-back.
 template <class C>
 __device__ __forceinline__ void tc_dft16(float2* v, TcCtx& tc) {
-    constexpr bool kScaled = C::TC == 1;  // FP16 operands
     const int tid = threadIdx.x;
     const int row = tid & 127;
     float up = 1.0f;
-    if constexpr (kScaled) {
+    if constexpr (C::kTcRowScale) {
         float mx = 0.0f;
 #pragma unroll
         for (int i = 0; i < 16; ++i) mx = fmaxf(mx, fmaxf(fabsf(v[i].x), fabsf(v[i].y)));
@@ -691,9 +705,73 @@ __device__ __forceinline__ void tc_dft16(float2* v, TcCtx& tc) {
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
         v[q] = make_float2(__uint_as_float(r[q]), __uint_as_float(r[16 + q]));
-        if constexpr (kScaled) v[q] = make_float2(v[q].x * up, v[q].y * up);
+        if constexpr (C::kTcRowScale) v[q] = make_float2(v[q].x * up, v[q].y * up);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+
+// FP16 tensor-core stages of signals spanning warps (kTcSignalScale):
+// per-signal power-of-two normalisation.  Before its first stage a signal is
+// multiplied by 2^-e, e taken from the largest |Re|, |Im| over the whole
+// signal, so that component lies in [1/2, 1); with
+// B = F / 16 no tensor-core stage can grow the largest modulus
+// (|F x|_inf <= 16 |x|_inf) and the FP32 radix-8 stages and twiddles grow it
+// by at most 8, so every FP16 operand stays below 8 sqrt(2).  The store
+// multiplies by 2^(e + 4k) for k tensor-core stages.  All factors are powers
+// of two, so they commute with the FP16 rounding (normal range).
+template <class C>
+__device__ __forceinline__ void tc_scale(float2 (&v)[C::E], int e) {
+    const float down = exp2i(-e);
+#pragma unroll
+    for (int i = 0; i < C::E; ++i) v[i] = make_float2(v[i].x * down, v[i].y * down);
+}
+
+// Step 1, right after a tile's stage-0 inputs are in registers (every thread
+// of the block calls it): each warp's maximum with one redux (non-negative
+// floats order like their bit patterns), published for step 2.
+template <class C>
+__device__ __forceinline__ void tc_norm_begin(float2 (&v)[C::E], TcCtx& tc) {
+    if constexpr (C::kTcSignalScale) {
+        float m = 0.0f;
+#pragma unroll
+        for (int i = 0; i < C::E; ++i) m = fmaxf(m, fmaxf(fabsf(v[i].x), fabsf(v[i].y)));
+        m = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(m)));
+        if ((threadIdx.x & 31) == 0) tc.red[threadIdx.x >> 5] = m;
+    }
+}
+
+// Step 2: after the block barrier that follows step 1 and before the next
+// one, read the signal's warp maxima and scale v.
+template <class C>
+__device__ __forceinline__ void tc_norm_end(float2 (&v)[C::E], TcCtx& tc) {
+    if constexpr (C::kTcSignalScale) {
+        constexpr int W = C::T / 32;  // warps per signal
+        const float* r = tc.red + (threadIdx.x / C::T) * W;
+        float m = r[0];
+#pragma unroll
+        for (int i = 1; i < W; ++i) m = fmaxf(m, r[i]);
+        tc.e = pow2_exponent(m);
+        tc_scale<C>(v, tc.e);
+    }
+}
+
+// The factor the last stage's outputs are stored with: `scale`, times
+// 2^(e + 4k) for a signal scaled as a whole; the rare excess beyond the
+// normal float range is applied to v here first.
+template <class C>
+__device__ __forceinline__ float tc_store_factor(float2 (&v)[C::E], const TcCtx& tc, float scale) {
+    if constexpr (!C::kTcSignalScale) {
+        return scale;
+    } else {
+        int ex = tc.e + 4 * C::kTcStages;  // in [-120, 126 + 16]
+        if (ex > 120) {
+            const float hi = exp2i(ex - 120);
+#pragma unroll
+            for (int i = 0; i < C::E; ++i) v[i] = make_float2(v[i].x * hi, v[i].y * hi);
+            ex = 120;
+        }
+        return scale * exp2i(ex);
+    }
 }
 
 // Butterfly handled by thread t in slot c of stage s.  The first and the last
@@ -961,6 +1039,7 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
         const int64_t sig = tile * C::S + sl;
         float2 v[C::E];
         gather_tile<C, INV>(v, ring + slot * TILE, sb, t);
+        tc_norm_begin<C>(v, tc);
         twist_and_dft<C, 0>(v, t, tw, tc);
         float2* b = smem + buf * TILE;
         if constexpr (C::kBuffers == 1) __syncthreads();  // previous readers of b are done
@@ -973,11 +1052,13 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
             }
         }
         gather<C, 1>(v, b, sb, t);
+        tc_norm_end<C>(v, tc);  // signals spanning warps: maxima published before the barrier
         if constexpr (C::kBuffers == 2) buf ^= 1;
         twist_and_dft<C, 1>(v, t, tw, tc);
         rest_stages<C, 2>(v, smem, buf, sb, t, tw, tc);
         const bool active = sig < batch && !dead && !tc.dead;
-        store_last<C, INV>(v, out + sig * C::N, t, active, scale);
+        const float f = tc_store_factor<C>(v, tc, scale);
+        store_last<C, INV>(v, out + sig * C::N, t, active, f);
     }
     if (tid == 0) inflight.drain(bars, wait_ns);  // copies in flight after a wait gave up
     if constexpr (C::TC != 0) tc_teardown<C>(tc);
@@ -1074,6 +1155,7 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
         const int64_t sig = tile * C::S + sl;
         float2 v[C::E];
         gather_tile<C, INV>(v, b, sb, t);
+        tc_norm_begin<C>(v, tc);
         twist_and_dft<C, 0>(v, t, tw, tc);
         // order this thread's generic accesses of the previous tile's slot
         // before the bulk copy that refills it, then one barrier: every thread
@@ -1083,13 +1165,15 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
         if (tid == 0 && it > 0 && !dead && !stall) {
             if (tile + (int64_t)(D - 1) * gridDim.x < ntiles) issue(it - 1 + D);
         }
+        tc_norm_end<C>(v, tc);  // signals spanning warps: maxima published before the barrier
         scatter<C, 0>(v, b, sb, t);
         __syncthreads();
         gather<C, 1>(v, b, sb, t);
         twist_and_dft<C, 1>(v, t, tw, tc);
         rest_stages_in_ring<C, 2>(v, b, sb, t, tw, tc);
         const bool active = sig < batch && !dead && !tc.dead;
-        store_last<C, INV>(v, out + sig * C::N, t, active, scale);
+        const float f = tc_store_factor<C>(v, tc, scale);
+        store_last<C, INV>(v, out + sig * C::N, t, active, f);
     }
     if (tid == 0) inflight.drain(bars, wait_ns);  // copies in flight after a wait gave up
     if constexpr (C::TC != 0) tc_teardown<C>(tc);
