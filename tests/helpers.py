@@ -55,3 +55,36 @@ def c32_max_stored(stored: torch.Tensor) -> np.ndarray:
 def c32_to(x: torch.Tensor, device) -> torch.Tensor:
     """Move a complex32 tensor (through its binary16 view)."""
     return x.contiguous().view(torch.float16).to(device).view(torch.complex32)
+
+
+def every_signal_violations(x: torch.Tensor, y: torch.Tensor, tol: float,
+                            chunk_elems: int = 1 << 24) -> torch.Tensor:
+    """Check every signal of a forward transform y = F x (device tensors
+    [batch, n], any complex dtype) against three consequences of the parity
+    bar ||y - X|| <= tol ||X|| (X the exact DFT; absolute tol where X = 0):
+
+    * Parseval, ||X|| = sqrt(N) ||x||, so | ||y|| - sqrt(N) ||x|| | <= bound;
+    * bin 0 of Eq. (dft) is the plain sum of x: |y_0 - sum x| <= bound;
+    * bin N/2 is the alternating sum: |y_{N/2} - sum (-1)^n x_n| <= bound
+      (any one component's error is at most the L2 norm of the error).
+
+    Sums run in FP64 on the device, from the input alone, a chunk of rows at a
+    time.  Returns the indices of the signals that break any of them."""
+    batch, n = x.shape
+    sign = torch.ones(n, dtype=torch.float64, device=x.device)
+    sign[1::2] = -1.0
+    rows = max(1, chunk_elems // n)
+    bad = []
+    for r0 in range(0, batch, rows):
+        xd = x[r0:r0 + rows].to(torch.complex128)
+        yd = y[r0:r0 + rows].to(torch.complex128)
+        ref_norm = torch.linalg.vector_norm(xd, dim=1) * (n ** 0.5)
+        bound = torch.where(ref_norm > 0, tol * ref_norm, torch.full_like(ref_norm, tol))
+        bound = bound * (1 + 1e-9) + 1e-300  # FP64 summation slack
+        ok = (torch.linalg.vector_norm(yd, dim=1) - ref_norm).abs() <= bound
+        ok &= (yd[:, 0] - xd.sum(dim=1)).abs() <= bound
+        if n >= 2:
+            ok &= (yd[:, n // 2] - (xd * sign).sum(dim=1)).abs() <= bound
+        bad.append(torch.nonzero(~ok).flatten() + r0)
+        del xd, yd
+    return torch.cat(bad).cpu() if bad else torch.empty(0, dtype=torch.int64)

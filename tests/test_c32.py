@@ -15,8 +15,8 @@ import torch
 
 import oracle
 import synth
-from tests.helpers import (FP32_TOL, c32_decode, c32_encode, c32_max_stored, c32_to, max_rel_l2,
-                           rel_l2_per_signal)
+from tests.helpers import (FP32_TOL, c32_decode, c32_encode, c32_max_stored, c32_to, every_signal_violations,
+                           max_rel_l2, rel_l2_per_signal)
 
 pytestmark = pytest.mark.gpu
 
@@ -146,7 +146,8 @@ def test_exact_and_degenerate_signals():
 @pytest.mark.parametrize("n", [256, 2048])
 def test_full_size_sampled(n):
     """The benchmark's complex32 workload: N * batch = 2^28 elements (1 GiB in),
-    U[-1, 1] (seed n) encoded to complex32; 256 seeded signals checked."""
+    U[-1, 1] (seed n) encoded to complex32; 256 seeded signals checked against
+    the oracle, every signal against Parseval and the bins 0 and N/2."""
     batch = 2 ** 28 // n
     x = synth.uniform(batch, n, seed=n, device="cuda")
     xs, xe = c32_encode_device(x)
@@ -161,6 +162,17 @@ def test_full_size_sampled(n):
     xin = c32_decode(pick(xs), xe.index_select(0, idx))
     got = c32_decode(pick(ys), ye.index_select(0, idx))
     assert max_rel_l2(got, oracle.reference(xin, threads=8)) <= C32_TOL
+    bad = every_signal_violations(c32_decode_c64(xs, xe), c32_decode_c64(ys, ye), C32_TOL)
+    assert bad.numel() == 0, bad[:8]
+
+
+def c32_decode_c64(stored: torch.Tensor, exp: torch.Tensor) -> torch.Tensor:
+    """complex32 storage decoded on the device to complex64: exact while the
+    exponents keep every value inside FP32's normal range."""
+    assert int(exp.abs().max()) < 100
+    h = stored.view(torch.float16).reshape(stored.shape[0], -1, 2).float()
+    h = h * torch.pow(2.0, exp.float())[:, None, None]
+    return torch.view_as_complex(h)
 
 
 def c32_encode_device(x: torch.Tensor):

@@ -11,7 +11,7 @@ import torch
 
 import oracle
 import synth
-from tests.helpers import FP32_TOL, max_rel_l2, to_np
+from tests.helpers import FP32_TOL, every_signal_violations, max_rel_l2, to_np
 from tests.oracle_pins import ramp_closed_form
 
 pytestmark = pytest.mark.gpu
@@ -262,7 +262,8 @@ def test_variant_selection():
 def test_full_size_sampled(n):
     """The benchmark's workload: N * batch = 2^28 complex64 (2 GiB in), U[-1,1]
     drawn on the device, launched exactly as the benchmark launches it; a
-    seeded sample of signals (first, last and random) is checked."""
+    seeded sample of signals (first, last and random) is checked against the
+    oracle, and every signal against Parseval and the bins 0 and N/2."""
     batch = 2 ** 28 // n
     x = synth.uniform(batch, n, seed=1, device="cuda")
     out = torch.empty_like(x)
@@ -276,6 +277,8 @@ def test_full_size_sampled(n):
     xs = x.index_select(0, ti).cpu()
     ys = to_np(out.index_select(0, ti))
     assert max_rel_l2(ys, oracle_of(xs)) <= FP32_TOL
+    bad = every_signal_violations(x, out, FP32_TOL)
+    assert bad.numel() == 0, bad[:8]
     plan.close()
     del x, out
     torch.cuda.empty_cache()
@@ -285,7 +288,8 @@ def test_full_size_sampled(n):
 def test_beyond_2_32_elements(n):
     """One call over more than 2^32 complex64 elements (34 GB in, 34 GB out):
     64-bit signal and element indexing in every kernel of the length; the
-    signals on both sides of element 2^32 and the last ones are checked."""
+    signals on both sides of element 2^32 and the last ones are checked against
+    the oracle, every signal against Parseval and the bins 0 and N/2."""
     batch = (2 ** 32) // n + 3
     if torch.cuda.mem_get_info()[0] < 2 * 8 * n * batch + (4 << 30):
         pytest.skip("needs about 70 GB of free device memory")
@@ -302,8 +306,10 @@ def test_beyond_2_32_elements(n):
     ti = torch.from_numpy(idx).cuda()
     xs = x.index_select(0, ti).cpu()
     ys = to_np(out.index_select(0, ti))
+    bad = every_signal_violations(x, out, FP32_TOL)
     del x, out
     torch.cuda.empty_cache()
+    assert bad.numel() == 0, bad[:8]
     assert max_rel_l2(ys, oracle_of(xs)) <= FP32_TOL
 
 

@@ -11,7 +11,7 @@ import torch
 
 import oracle
 import synth
-from tests.helpers import max_rel_l2, rel_l2_per_signal, to_np
+from tests.helpers import every_signal_violations, max_rel_l2, rel_l2_per_signal, to_np
 
 pytestmark = pytest.mark.gpu
 
@@ -47,7 +47,8 @@ def test_tc_against_oracle(n, dtype, inverse):
 @pytest.mark.parametrize("n", [256, 2048])
 def test_precision_workload_sample(n, dtype):
     """N in {256, 2048}, batch 2^17, as the benchmark runs it; a seeded sample
-    of signals (first, last, random) against the oracle."""
+    of signals (first, last, random) against the oracle, every signal against
+    Parseval and the bins 0 and N/2."""
     batch = 2 ** 17
     x, _ = synth.scaled_normal(batch, n, seed=4, device="cuda")
     out, _ = run(x, n, dtype)
@@ -55,6 +56,8 @@ def test_precision_workload_sample(n, dtype):
     idx = torch.from_numpy(np.unique(np.concatenate([[0, batch - 1], rng.integers(0, batch, 254)]))).cuda()
     want = oracle.reference(x.index_select(0, idx).cpu().numpy(), threads=8)
     assert max_rel_l2(to_np(out.index_select(0, idx)), want) <= TC_TOL
+    bad = every_signal_violations(x, out, TC_TOL)
+    assert bad.numel() == 0, bad[:8]
 
 
 @pytest.mark.parametrize("dtype", ["tc_f16", "tc_bf16"])
