@@ -413,16 +413,23 @@ def run_reference(args):
         cpu_baseline(budget_s=budget / 4)
     vals = []
     cb = None
+    t0 = time.perf_counter()
     for _ in range(args.steps):
         cb = cpu_baseline(budget_s=budget)
         vals.append(cb["value"])
+    sample_ms = (time.perf_counter() - t0) * 1e3 / max(args.steps, 1)
     value = statistics.mean(vals)
     cb["value"] = round(value, 4)
+    # one full step (every length over ELEMS elements) at the sampled rate, so
+    # that value * ms_per_step is the step's bytes on both arms
+    full_step_ms = BYTES_PER_ELEM * ELEMS * len(LOG2NS) / (value * 1e9) * 1e3
     line = {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "GB/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD + " (bounded CPU sample per step)", "device": "host cpu"},
+            "ms_per_step": round(full_step_ms, 1), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD + " (bounded CPU sample per step)", "device": "host cpu",
+                       "ms_per_step": "one full step's bytes at the sampled rate",
+                       "sample_ms_per_step": round(sample_ms, 1)},
             "cpu_baseline": cb,
             "e2e": {"value": round(value, 4), "unit": "GB/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}

@@ -76,3 +76,21 @@ def test_cpu_baseline_line_is_bounded_and_complete():
     assert cb["kind"] == "oracle" and cb["unit"] == "GB/s" and cb["cores"] == 2
     assert cb["value"] > 0 and set(cb["per_n_gbs"]) == {str(2 ** k) for k in bench.LOG2NS}
     assert "M elements" in cb["sample"]
+
+
+def test_reference_line_keys(monkeypatch, capsys):
+    """The reference arm's JSON line: the contract keys, a full-step time that
+    matches its rate, and a zero-byte e2e."""
+    fake = {"value": 8.0, "unit": "GB/s", "cores": 4, "kind": "oracle", "sample": "x", "per_n_gbs": {}}
+    monkeypatch.setattr(bench, "cpu_baseline", lambda budget_s=0, threads=None: dict(fake))
+    monkeypatch.delenv("RANK", raising=False)
+    args = type("A", (), {"steps": 2, "warmup": 3})()
+    assert bench.run_reference(args) == 0
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    for k in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+              "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in line, k
+    assert line["impl"] == "reference" and line["value"] == 8.0
+    step_bytes = bench.BYTES_PER_ELEM * bench.ELEMS * len(bench.LOG2NS)
+    assert abs(line["value"] * 1e9 * line["ms_per_step"] * 1e-3 - step_bytes) / step_bytes < 1e-3
+    assert line["e2e"] == {"value": 8.0, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
