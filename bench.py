@@ -182,6 +182,13 @@ def cpu_baseline(budget_s: float = 12.0, threads: int | None = None):
             "per_n_gbs": detail}
 
 
+def sample_stats(ms: list) -> dict:
+    """Mean, median, minimum ("optimal") and standard deviation of per-call or
+    per-step times (ms)."""
+    return {"mean": round(statistics.mean(ms), 4), "median": round(statistics.median(ms), 4),
+            "min": round(min(ms), 4), "std": round(statistics.pstdev(ms), 4)}
+
+
 def tc_stage_count(info) -> int:
     """Radix-16 stages a plan runs on tensor cores (0 for an FP32 plan)."""
     if info.tc == 0:
@@ -530,6 +537,7 @@ def run_ours(args):
     ms = t_start.elapsed_time(t_end)
     per_launch = {k: [ev[s][i][0].elapsed_time(ev[s][i][1]) for s in range(args.steps)]
                   for i, k in enumerate(LOG2NS)}
+    per_step = [ev[s][0][0].elapsed_time(ev[s][-1][1]) for s in range(args.steps)]
     ms = reduce_max_over_ranks(ms, dev)
     # correctness spot check of the timed output (last length) before reporting
     assert all(p.error() == 0 for p in plans.values())
@@ -587,9 +595,12 @@ def run_ours(args):
     for k in LOG2NS:
         avg = statistics.mean(per_launch[k])
         gbs = len_bytes[k] / (avg * 1e-3) / 1e9
+        st = sample_stats(per_launch[k])
         per_n[str(2 ** k)] = {"ms": round(avg, 4), "gbs": round(gbs, 1),
                               "frac": round(gbs / peak, 4),
-                              "gflops": round(ELEMS * flops_per_elem(2 ** k) / (avg * 1e-3) / 1e9, 1)}
+                              "gflops": round(ELEMS * flops_per_elem(2 ** k) / (avg * 1e-3) / 1e9, 1),
+                              "ms_median": st["median"], "ms_min": st["min"], "ms_std": st["std"],
+                              "gbs_best": round(len_bytes[k] / (st["min"] * 1e-3) / 1e9, 1)}
     dom = max(LOG2NS, key=lambda k: statistics.mean(per_launch[k]))
     dom_ms = statistics.mean(per_launch[dom])
     achieved = len_bytes[dom] / (dom_ms * 1e-3) / 1e9
@@ -605,7 +616,8 @@ def run_ours(args):
                    "elements_per_length": ELEMS, "bytes_per_step_per_gpu": step_bytes,
                    "l2": ("inputs 1 GiB per length (complex32), 8x L2: no flush needed" if c32
                           else "inputs 2 GiB per length, 16x L2: no flush needed"),
-                   "parallelism": f"replicas x{world}", "per_n": per_n},
+                   "parallelism": f"replicas x{world}", "step_ms": sample_stats(per_step),
+                   "per_n": per_n},
         "roofline": {"bound": "hbm", "kernel": f"fft N={2 ** dom}", "achieved": round(achieved, 1),
                      "peak": peak, "peak_source": peak_src, "unit": "GB/s",
                      "frac": round(achieved / peak, 4),

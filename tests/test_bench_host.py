@@ -94,3 +94,9 @@ def test_reference_line_keys(monkeypatch, capsys):
     step_bytes = bench.BYTES_PER_ELEM * bench.ELEMS * len(bench.LOG2NS)
     assert abs(line["value"] * 1e9 * line["ms_per_step"] * 1e-3 - step_bytes) / step_bytes < 1e-3
     assert line["e2e"] == {"value": 8.0, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_sample_stats():
+    st = bench.sample_stats([2.0, 1.0, 4.0, 3.0])
+    assert st == {"mean": 2.5, "median": 2.5, "min": 1.0, "std": round(1.25 ** 0.5, 4)}
+    assert bench.sample_stats([0.5]) == {"mean": 0.5, "median": 0.5, "min": 0.5, "std": 0.0}
