@@ -18,8 +18,9 @@
 // E/R butterflies per stage.  Stage 0 reads straight from HBM and the last
 // stage writes straight to HBM, with 128-bit accesses whenever a thread owns
 // two neighbouring butterflies; stages exchange through shared memory with an
-// XOR swizzle that makes every exchange bank-conflict free.  A persistent
-// grid-stride loop walks tiles of S signals.
+// XOR swizzle (conflict free for N = 128, 256, 1024, 2048; 1.25x the minimum
+// wavefronts at N = 512 and 1.5x at N = 32 and 64, where HBM still bounds the
+// kernel).  A persistent grid-stride loop walks tiles of S signals.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -239,8 +240,9 @@ __device__ __forceinline__ void st_stream4v(float4* p, float4 a) {
 }
 
 // Shared-memory swizzle at 8-byte granularity: rows of 16 elements (128 B)
-// are XOR-permuted by their row index.  Keeps every Stockham exchange of the
-// schedules below conflict free (checked by an index model on the host).
+// are XOR-permuted by their row index.  tests/test_bank_model.py replays every
+// schedule's exchanges under it and counts the wavefronts (64-bit accesses
+// resolve per half-warp), in agreement with ncu.
 __device__ __forceinline__ int swz8(int a) { return a ^ ((a >> 4) & 15); }
 // Same idea at 16-byte granularity (rows of 8 float4 slots).
 __device__ __forceinline__ int swz16(int a) { return a ^ ((a >> 3) & 7); }
@@ -776,7 +778,7 @@ __device__ __forceinline__ float tc_store_factor(float2 (&v)[C::E], const TcCtx&
 
 // Butterfly handled by thread t in slot c of stage s.  The first and the last
 // stage give a thread neighbouring butterflies (vectorised HBM access); the
-// middle stages interleave threads (coalesced, conflict-free exchanges).
+// middle stages interleave threads (coalesced exchanges).
 template <class C, int s>
 __device__ __forceinline__ int bfly(int t, int c) {
     constexpr int K = C::E / C::radix(s);

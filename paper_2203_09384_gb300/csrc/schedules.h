@@ -24,9 +24,10 @@
 //           evict-first); the defaults are the measured best per length)
 // Threads per block = S * N / E.  Stage 0 with R0 = E/2 (and the last stage,
 // where its radix is E/2 or less) lets a thread own neighbouring butterflies,
-// so its HBM accesses are 128-bit.  An index model on the host checked the
-// shared-memory exchanges of every row for bank conflicts under the XOR
-// swizzle of fft_device.cuh (64-bit accesses resolve per half-warp).
+// so its HBM accesses are 128-bit.  tests/test_bank_model.py replays the
+// shared-memory exchanges of every row under the XOR swizzle of
+// fft_device.cuh and counts their bank conflicts (64-bit accesses resolve per
+// half-warp).
 //
 // One-thread-per-signal rows (N <= 32): SX(log2N, variant, warps per block,
 // 32-signal groups per warp tile, cache hints as CH above).

@@ -100,3 +100,12 @@ def test_sample_stats():
     st = bench.sample_stats([2.0, 1.0, 4.0, 3.0])
     assert st == {"mean": 2.5, "median": 2.5, "min": 1.0, "std": round(1.25 ** 0.5, 4)}
     assert bench.sample_stats([0.5]) == {"mean": 0.5, "median": 0.5, "min": 0.5, "std": 0.0}
+
+
+def test_source_hash_ignores_comments_only():
+    code = 'int f(int a) { // twice\n  return 2 * a; /* doubled */ }\nconst char* s = "x // y";\n'
+    same = '/* header */\nint f(int a) {\n    return 2 * a;  // edited comment\n}\nconst char* s = "x // y";'
+    assert bench.strip_comments(code) == bench.strip_comments(same)
+    assert bench.strip_comments(code) != bench.strip_comments(code.replace("2 * a", "3 * a"))
+    assert bench.strip_comments(code) != bench.strip_comments(code.replace('"x // y"', '"x // z"'))
+
