@@ -117,10 +117,10 @@ GBFFT_API fft_status_t fft_plan_create(int64_t n, int64_t batch, int direction, 
  * device work list; fft_execute then launches ONE persistent kernel whose
  * blocks take tiles from the list (graph-capturable).  Variants that share
  * the tiles through a work counter clear it first with a memset node; because
- * of that counter, a ragged plan must not be executed on two streams at once.  flags: FFT_FLAG_UNNORMALIZED,
- * FFT_FLAG_SCALE_FORWARD, FFT_FLAG_VARIANT(k) with k < fft_ragged_variant_count()
- * (without it: variant 6, a producer warp filling ring slots for 128 compute
- * threads per block).
+ * of that counter, a ragged plan must not be executed on two streams at once.
+ * flags: FFT_FLAG_UNNORMALIZED, FFT_FLAG_SCALE_FORWARD, FFT_FLAG_VARIANT(k)
+ * with k < fft_ragged_variant_count() (without it: variant 6, a producer warp
+ * filling ring slots for 128 compute threads per block).
  * Errors: FFT_ERR_INVALID_SIZE (a length), FFT_ERR_INVALID_VALUE, FFT_ERR_MISALIGNED
  * (odd offsets_host[0]), FFT_ERR_ALLOC, FFT_ERR_CUDA, FFT_ERR_NO_DEVICE.
  */
