@@ -1,11 +1,12 @@
 """Autotuner for the schedule variants (tile shape, radix split, prefetch).
 
 For each transform length the library compiles several schedules (see
-csrc/schedules.h); for ragged batches it compiles two work-list kernels.
-This module times every candidate on the device with CUDA events on a
-synthetic batch of the requested shape, keeps the fastest, makes it the
-default through the C-ABI (fft_set_default_variant) and records the choice
-in a JSON cache keyed by GPU name and library version, so later processes
+csrc/schedules.h); for ragged batches it compiles several work-list
+kernels (fft_ragged_variant_count).  This module times every candidate on
+the device with CUDA events on a synthetic batch of the requested shape,
+keeps the fastest, makes it the default through the C-ABI
+(fft_set_default_variant) and records the choice in a JSON cache keyed by
+GPU name, library version and the compiled variant table, so later processes
 start from the tuned table (load_cache) without re-measuring.
 
 Cache location: $GBFFT_TUNE_CACHE, else ~/.cache/gbfft/tune.json.
@@ -28,9 +29,17 @@ def cache_path() -> str:
         os.path.expanduser("~"), ".cache", "gbfft", "tune.json")
 
 
+def schedule_fingerprint() -> str:
+    """The compiled variant table as seen through the C-ABI (count and dtype of
+    every variant per length), so that a cached variant number is applied only
+    to the table it was measured on."""
+    return ";".join(f"{n}:" + "".join(str(_abi.fft_variant_dtype(n, v)) for v in range(_abi.fft_variant_count(n)))
+                    for n in LENGTHS) + f";r{_abi.fft_ragged_variant_count()}"
+
+
 def _device_key(device=None) -> str:
     name = torch.cuda.get_device_name(device)
-    return f"{name}|{_abi.lib().fft_version().decode()}"
+    return f"{name}|{_abi.lib().fft_version().decode()}|{schedule_fingerprint()}"
 
 
 def _time(fn, reps: int, warmup: int = 2) -> float:
@@ -127,6 +136,8 @@ def load_cache(path=None, device=None) -> dict:
     except (OSError, ValueError):
         return {}
     for n, v in entry.get("plain", {}).items():
-        if 0 <= int(v) < _abi.fft_variant_count(int(n)):
-            _abi.fft_set_default_variant(int(n), int(v))
+        n, v = int(n), int(v)
+        # only FP32 complex64 schedules can be a length's default
+        if 0 <= v < _abi.fft_variant_count(n) and _abi.fft_variant_dtype(n, v) == _abi.FFT_C64:
+            _abi.fft_set_default_variant(n, v)
     return entry
