@@ -35,6 +35,27 @@ __all__ = ["Plan", "RaggedPlan", "fft", "ifft", "FFTFunction", "IFFTFunction", "
 _DTYPES = {"c64": FFT_C64, "tc_f16": FFT_C64_TC_F16, "tc_bf16": FFT_C64_TC_BF16, "c32": FFT_C32}
 
 
+def _cuda_device(device) -> torch.device:
+    """The plan's device with an explicit index ("cuda" means the current one)."""
+    d = torch.device(device) if device is not None else torch.device("cuda")
+    if d.type != "cuda":
+        raise ValueError(f"plans live on a CUDA device, got {d}")
+    return d if d.index is not None else torch.device("cuda", torch.cuda.current_device())
+
+
+def _check_buffer(t: torch.Tensor, name: str, dtype, device, numel: int, at_least: bool = False) -> None:
+    """A buffer handed to the C-ABI as a bare pointer: the library cannot see
+    its size, dtype or device, so they are checked here before the launch."""
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if t.device != device:
+        raise ValueError(f"{name} is on {t.device}, expected {device}")
+    if (t.numel() < numel) if at_least else (t.numel() != numel):
+        raise ValueError(f"{name} has {t.numel()} elements, needs {'at least ' if at_least else ''}{numel}")
+
+
 class Plan:
     """One planned transform: length ``n``, ``batch`` signals, a direction.
 
@@ -49,8 +70,7 @@ class Plan:
         self.n, self.batch, self.inverse = int(n), int(batch), bool(inverse)
         self.dtype = dtype
         self.normalized = normalized
-        self.device = torch.device(device) if device is not None else torch.device(
-            "cuda", torch.cuda.current_device())
+        self.device = _cuda_device(device)
         flags = 0 if normalized else FFT_FLAG_UNNORMALIZED
         if scale_forward and not inverse:
             flags |= FFT_FLAG_SCALE_FORWARD
@@ -68,16 +88,11 @@ class Plan:
         return fft_plan_get_info(self.handle)
 
     def execute(self, x: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
-        if x.dtype != torch.complex64 or not x.is_cuda:
-            raise TypeError("expected a complex64 CUDA tensor")
-        if not x.is_contiguous():
-            raise ValueError("expected a contiguous tensor")
-        if x.numel() != self.n * self.batch:
-            raise ValueError(f"tensor has {x.numel()} elements, plan wants {self.n * self.batch}")
+        _check_buffer(x, "x", torch.complex64, self.device, self.n * self.batch)
         if out is None:
             out = torch.empty_like(x)
-        elif out.dtype != torch.complex64 or not out.is_contiguous() or out.numel() != x.numel():
-            raise ValueError("out must be a contiguous complex64 tensor like x")
+        else:
+            _check_buffer(out, "out", torch.complex64, self.device, self.n * self.batch)
         with torch.cuda.device(x.device):
             s = stream if stream is not None else torch.cuda.current_stream(x.device)
             fft_execute(self.handle, x.data_ptr(), out.data_ptr(), s.cuda_stream)
@@ -88,31 +103,31 @@ class Plan:
         """complex32 storage (plan dtype "c32"): x is a torch.complex32 CUDA
         tensor, x_exp an int8 tensor of one exponent per signal (value =
         stored * 2^exp).  Returns (out, out_exp) in the same representation."""
-        if x.dtype != torch.complex32 or not x.is_cuda or not x.is_contiguous():
-            raise TypeError("expected a contiguous complex32 CUDA tensor")
-        if x.numel() != self.n * self.batch or x_exp.numel() != self.batch or x_exp.dtype != torch.int8:
-            raise ValueError("shape mismatch: x needs n*batch elements, x_exp batch int8")
+        _check_buffer(x, "x", torch.complex32, self.device, self.n * self.batch)
+        _check_buffer(x_exp, "x_exp", torch.int8, self.device, self.batch)
         if out is None:
             out = torch.empty_like(x)
-        elif out.dtype != torch.complex32 or not out.is_contiguous() or out.numel() != x.numel():
-            raise ValueError("out must be a contiguous complex32 tensor like x")
+        else:
+            _check_buffer(out, "out", torch.complex32, self.device, self.n * self.batch)
         if out_exp is None:
             out_exp = torch.empty(self.batch, dtype=torch.int8, device=x.device)
+        else:
+            _check_buffer(out_exp, "out_exp", torch.int8, self.device, self.batch)
         with torch.cuda.device(x.device):
             s = stream if stream is not None else torch.cuda.current_stream(x.device)
-            fft_execute_c32(self.handle, x.data_ptr(), x_exp.contiguous().data_ptr(), out.data_ptr(),
+            fft_execute_c32(self.handle, x.data_ptr(), x_exp.data_ptr(), out.data_ptr(),
                             out_exp.data_ptr(), s.cuda_stream)
         return out, out_exp
 
     def execute_host(self, x: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
         """Transform a host (CPU, ideally pinned) tensor through the plan's
         chunked copy/transform/copy pipeline; synchronises the stream."""
-        if x.dtype != torch.complex64 or x.is_cuda or not x.is_contiguous():
-            raise TypeError("expected a contiguous complex64 CPU tensor")
-        if x.numel() != self.n * self.batch:
-            raise ValueError(f"tensor has {x.numel()} elements, plan wants {self.n * self.batch}")
+        cpu = torch.device("cpu")
+        _check_buffer(x, "x", torch.complex64, cpu, self.n * self.batch)
         if out is None:
             out = torch.empty(x.shape, dtype=x.dtype, pin_memory=x.is_pinned())
+        else:
+            _check_buffer(out, "out", torch.complex64, cpu, self.n * self.batch)
         with torch.cuda.device(self.device):
             s = stream if stream is not None else torch.cuda.current_stream(self.device)
             fft_execute_host(self.handle, x.data_ptr(), out.data_ptr(), s.cuda_stream)
@@ -150,8 +165,7 @@ class RaggedPlan:
         self.count = len(offs) - 1
         self.total = offs[-1]
         self.inverse = inverse
-        self.device = torch.device(device) if device is not None else torch.device(
-            "cuda", torch.cuda.current_device())
+        self.device = _cuda_device(device)
         flags = 0 if normalized else FFT_FLAG_UNNORMALIZED
         if scale_forward and not inverse:
             flags |= FFT_FLAG_SCALE_FORWARD
@@ -166,12 +180,11 @@ class RaggedPlan:
         return fft_plan_get_info(self.handle)
 
     def execute(self, x: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
-        if x.dtype != torch.complex64 or not x.is_cuda or not x.is_contiguous():
-            raise TypeError("expected a contiguous complex64 CUDA tensor")
-        if x.numel() < self.total:
-            raise ValueError(f"buffer has {x.numel()} elements, offsets reach {self.total}")
+        _check_buffer(x, "x", torch.complex64, self.device, self.total, at_least=True)
         if out is None:
             out = torch.empty_like(x)
+        else:
+            _check_buffer(out, "out", torch.complex64, self.device, self.total, at_least=True)
         with torch.cuda.device(x.device):
             s = stream if stream is not None else torch.cuda.current_stream(x.device)
             fft_execute(self.handle, x.data_ptr(), out.data_ptr(), s.cuda_stream)

@@ -198,6 +198,16 @@ def test_rejects_misaligned_and_overlapping():
     assert L.fft_execute(plan.handle, base, base + 16, None) == _abi.STATUS_CODE["FFT_ERR_OVERLAP"]
     assert L.fft_execute(plan.handle, None, base, None) == _abi.STATUS_CODE["FFT_ERR_INVALID_VALUE"]
     torch.cuda.synchronize()
+    # the binding checks what the bare pointers cannot carry: size, dtype, device
+    x = torch.zeros(batch, n, dtype=torch.complex64, device="cuda")
+    with pytest.raises(ValueError):
+        plan.execute(x, torch.empty(batch * n - 1, dtype=torch.complex64, device="cuda"))
+    with pytest.raises(ValueError):
+        plan.execute(x, torch.empty(batch, n, dtype=torch.complex64))
+    with pytest.raises(ValueError):
+        plan.execute(x.cpu())
+    with pytest.raises(TypeError):
+        plan.execute(x.to(torch.complex128))
     plan.close()
 
 

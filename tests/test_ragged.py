@@ -155,6 +155,15 @@ def test_ragged_edge_cases():
     empty = gb.RaggedPlan([0])
     empty.execute(x, torch.empty_like(x))
     empty.close()
+    # the library sees bare pointers: a short or misplaced out is refused before launch
+    p = gb.RaggedPlan([0, 64])
+    with pytest.raises(ValueError):
+        p.execute(x, torch.empty(32, dtype=torch.complex64, device="cuda"))
+    with pytest.raises(ValueError):
+        p.execute(x, torch.empty(64, dtype=torch.complex64))
+    with pytest.raises(TypeError):
+        p.execute(x, torch.empty(64, dtype=torch.complex128, device="cuda"))
+    p.close()
     code = _abi.STATUS_CODE
     for offs, err in [([0, 12], "FFT_ERR_INVALID_SIZE"), ([0, 4096], "FFT_ERR_INVALID_SIZE"),
                       ([0, 1], "FFT_ERR_INVALID_SIZE"), ([1, 9], "FFT_ERR_MISALIGNED"),
