@@ -1,6 +1,8 @@
 """The public header is plain C: a C99 program compiles against
 include/gbfft.h, links libgbfft.so and gets the documented argument checks
-(no GPU needed for these calls)."""
+(no GPU needed for these calls), and its plan-info struct lays out as the
+ctypes binding reads it."""
+import ctypes
 import os
 import subprocess
 
@@ -52,3 +54,22 @@ def test_header_is_c99_and_links(tmp_path):
     assert r.returncode == 0, r.stderr
     out = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
     assert out.returncode == 0 and out.stdout.strip().endswith("OK"), out.stdout + out.stderr
+
+
+def test_plan_info_layout_matches_ctypes(tmp_path):
+    """The ctypes PlanInfo the binding reads must lay out exactly like the
+    header's fft_plan_info_t (size and every field offset, as gcc sees it)."""
+    fields = [name for name, _ in _abi.PlanInfo._fields_]
+    body = "\n".join(f'    printf("{f} %zu\\n", offsetof(fft_plan_info_t, {f}));' for f in fields)
+    src = tmp_path / "layout.c"
+    src.write_text('#include <stddef.h>\n#include <stdio.h>\n#include "gbfft.h"\nint main(void) {\n'
+                   '    printf("sizeof %zu\\n", sizeof(fft_plan_info_t));\n' + body + "\n    return 0;\n}\n")
+    exe = tmp_path / "layout"
+    r = subprocess.run(["gcc", "-std=c99", "-I", os.path.dirname(_abi.HEADER), str(src), "-o", str(exe)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    got = dict(line.split() for line in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                        timeout=60).stdout.splitlines())
+    assert int(got["sizeof"]) == ctypes.sizeof(_abi.PlanInfo)
+    for f in fields:
+        assert int(got[f]) == getattr(_abi.PlanInfo, f).offset, f
