@@ -27,7 +27,8 @@
 // so its HBM accesses are 128-bit.  tests/test_bank_model.py replays the
 // shared-memory exchanges of every row under the XOR swizzle of
 // fft_device.cuh and counts their bank conflicts (64-bit accesses resolve per
-// half-warp).
+// half-warp); tests/test_stockham_model.py replays every row's index mapping
+// on the CPU and checks that it computes the DFT.
 //
 // One-thread-per-signal rows (N <= 32): SX(log2N, variant, warps per block,
 // 32-signal groups per warp tile, cache hints as CH above).
