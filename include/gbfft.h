@@ -68,10 +68,10 @@ enum {
      * see fft_set_default_variant).  Build them with FFT_FLAG_VARIANT(k). */
     FFT_FLAG_VARIANT_MASK = 0xFu << 8,
     /* Test hook for failure detection: kernels with device-side waits (the
-     * bulk-copy ring, the tensor-core stages) issue nothing, so their bounded
-     * waits run out after the plan's wait limit and fft_plan_get_error
-     * reports FFT_ERR_TIMEOUT.  The output is not written.  Plans of kernels
-     * without device-side waits ignore it. */
+     * bulk-copy rings, the tensor-core stages, ragged variants 4..7) issue
+     * nothing, so their bounded waits run out after the plan's wait limit and
+     * fft_plan_get_error reports FFT_ERR_TIMEOUT.  The output is not written.
+     * Plans of kernels without device-side waits ignore it. */
     FFT_FLAG_TEST_STALL = 1u << 16,
     /* Give the plan device staging buffers (three chunks of about 64 MiB)
      * and three internal streams so that fft_execute_host can be used. */
@@ -118,9 +118,10 @@ GBFFT_API fft_status_t fft_plan_create(int64_t n, int64_t batch, int direction, 
  * blocks take tiles from the list (graph-capturable).  Variants that share
  * the tiles through a work counter clear it first with a memset node; because
  * of that counter, a ragged plan must not be executed on two streams at once.
- * flags: FFT_FLAG_UNNORMALIZED, FFT_FLAG_SCALE_FORWARD, FFT_FLAG_VARIANT(k)
- * with k < fft_ragged_variant_count() (without it: variant 6, a producer warp
- * filling ring slots for 128 compute threads per block).
+ * flags: FFT_FLAG_UNNORMALIZED, FFT_FLAG_SCALE_FORWARD, FFT_FLAG_TEST_STALL,
+ * FFT_FLAG_VARIANT(k) with k < fft_ragged_variant_count() (without it: the
+ * process-wide default of fft_set_default_ragged_variant, initially variant
+ * 6, a producer warp filling ring slots for 128 compute threads per block).
  * Errors: FFT_ERR_INVALID_SIZE (a length), FFT_ERR_INVALID_VALUE, FFT_ERR_MISALIGNED
  * (odd offsets_host[0]), FFT_ERR_ALLOC, FFT_ERR_CUDA, FFT_ERR_NO_DEVICE.
  */
@@ -129,6 +130,17 @@ GBFFT_API fft_status_t fft_plan_create_ragged(const int64_t* offsets_host, int64
 
 /* Number of compiled schedule variants of the ragged kernel. */
 GBFFT_API int fft_ragged_variant_count(void);
+
+/*
+ * The ragged variant that later fft_plan_create_ragged calls use when their
+ * flags name none (process-wide; plans already made keep theirs).  The
+ * autotuner applies its cached choice through this call.  Needs no GPU.
+ * Errors: FFT_ERR_INVALID_VALUE when variant is not in
+ * [0, fft_ragged_variant_count()).  fft_get_default_ragged_variant returns
+ * the current choice.
+ */
+GBFFT_API fft_status_t fft_set_default_ragged_variant(int variant);
+GBFFT_API int fft_get_default_ragged_variant(void);
 
 /* As fft_plan_create, with FFT_FLAG_* bits in `flags`. */
 GBFFT_API fft_status_t fft_plan_create_ex(int64_t n, int64_t batch, int direction, int dtype,
@@ -183,8 +195,15 @@ GBFFT_API fft_status_t fft_execute_host(fft_plan_t plan, const void* in_host, vo
 
 /*
  * Read and clear the plan's device error word (FFT_OK when no device-side
- * check fired).  Synchronises the plan's device; call it after the work you
- * want checked has been enqueued.
+ * check fired).  It first synchronises the plan's whole device
+ * (cudaDeviceSynchronize with that device current, the caller's current
+ * device restored afterwards), so work enqueued on any stream of that device
+ * before the call, non-blocking streams included, has finished and the word
+ * is final when it is read.  Call it after the work you want checked has been
+ * enqueued, and not while a stream of that device is being captured into a
+ * CUDA graph.  Returns FFT_ERR_CUDA if the synchronisation or the copy fails
+ * (for example after an earlier kernel fault), else the word: FFT_OK or the
+ * code a kernel recorded (FFT_ERR_TIMEOUT).
  */
 GBFFT_API fft_status_t fft_plan_get_error(fft_plan_t plan);
 
@@ -238,8 +257,8 @@ GBFFT_API int fft_variant_dtype(int64_t n, int variant);
 
 /*
  * Wall-time limit for the device-side waits of this plan's kernels (the
- * bulk-copy prefetch rings and the tensor-core MMA completion wait on
- * mbarriers).  A wait that runs out records FFT_ERR_TIMEOUT in the plan's
+ * bulk-copy prefetch rings, ragged variants 4..7 and the tensor-core MMA
+ * completion wait on mbarriers).  A wait that runs out records FFT_ERR_TIMEOUT in the plan's
  * error word (see fft_plan_get_error); the block then stops waiting and
  * issuing, skips its stores and finishes, after waiting once more (with the
  * same limit) for copies or MMAs it had already issued.  Default 4 s.  0 is
@@ -284,9 +303,13 @@ GBFFT_API fft_status_t fft_validate(int64_t n, int64_t batch, int direction, int
  *
  * Arguments: n, batch, direction as for fft_plan_create (dtype is FFT_C64);
  * flags may hold FFT_FLAG_UNNORMALIZED, FFT_FLAG_SCALE_FORWARD and
- * FFT_FLAG_VARIANT(k); in/out/stream as for fft_execute (device pointers,
- * 16-byte aligned, equal or disjoint; the caller owns them).  The result
- * equals fft_execute's for the same length, direction, flags and variant.
+ * FFT_FLAG_VARIANT(k) of an FP32 variant, any other bit is refused with
+ * FFT_ERR_INVALID_VALUE; in/out/stream as for fft_execute (device pointers,
+ * 16-byte aligned, equal or disjoint; the caller owns them).  The twiddle
+ * table is generated on the device by the same steps as the plan path's
+ * (quadrant fold, FP64 cos/sin, one rounding to FP32), and the same kernel
+ * runs, so the result is bit-identical to fft_execute's for the same length,
+ * direction, flags and variant (tested for every compiled FP32 schedule).
  *
  * Behaviour:
  *  - The first call on a device does a one-time set-up (it looks up the

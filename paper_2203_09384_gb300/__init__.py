@@ -12,6 +12,7 @@ built extension, calls raise.
 """
 from __future__ import annotations
 
+import collections
 import threading
 
 import torch
@@ -26,7 +27,8 @@ from ._abi import (FFT_C32, FFT_C64, FFT_C64_TC_BF16, FFT_C64_TC_F16, FFT_FLAG_S
                    fft_plan_create_ex, fft_plan_destroy, fft_plan_get_error, fft_plan_get_info,
                    fft_plan_set_wait_limit, FFT_FLAG_TEST_STALL, FFT_FLAG_HOST_STAGING,
                    fft_execute_host,
-                   fft_validate, lib)
+                   fft_validate, lib, fft_set_default_ragged_variant, fft_get_default_ragged_variant)
+from . import autotune  # noqa: E402
 
 __all__ = ["Plan", "RaggedPlan", "fft", "ifft", "FFTFunction", "IFFTFunction", "fft_plan_create",
            "fft_plan_create_ex", "fft_plan_create_ragged", "fft_execute", "fft_plan_destroy",
@@ -82,6 +84,7 @@ class Plan:
         direction = FFT_INVERSE if inverse else FFT_FORWARD
         self.handle = None
         with torch.cuda.device(self.device):
+            autotune.autoload(self.device)
             self.handle = fft_plan_create_ex(self.n, self.batch, direction, _DTYPES[dtype], flags)
 
     def info(self):
@@ -157,7 +160,8 @@ class RaggedPlan:
     of a flat complex64 buffer; one persistent launch transforms them all."""
 
     def __init__(self, offsets, inverse: bool = False, normalized: bool = True,
-                 scale_forward: bool = False, variant: int | None = None, device=None):
+                 scale_forward: bool = False, variant: int | None = None, device=None,
+                 extra_flags: int = 0):
         offs = [int(v) for v in (offsets.tolist() if hasattr(offsets, "tolist") else offsets)]
         if len(offs) < 1:
             raise ValueError("offsets needs count + 1 entries")
@@ -171,8 +175,10 @@ class RaggedPlan:
             flags |= FFT_FLAG_SCALE_FORWARD
         if variant is not None:
             flags |= FFT_FLAG_VARIANT(variant)
+        flags |= int(extra_flags)
         self.handle = None
         with torch.cuda.device(self.device):
+            autotune.autoload(self.device)
             self.handle = fft_plan_create_ragged(offs, FFT_INVERSE if inverse else FFT_FORWARD,
                                                  FFT_C64, flags)
 
@@ -203,6 +209,12 @@ class RaggedPlan:
             self.execute(x, out)
         return g
 
+    def error(self) -> int:
+        return fft_plan_get_error(self.handle)
+
+    def set_wait_limit(self, nanoseconds: int) -> None:
+        fft_plan_set_wait_limit(self.handle, nanoseconds)
+
     def close(self):
         if self.handle:
             fft_plan_destroy(self.handle)
@@ -215,8 +227,19 @@ class RaggedPlan:
             pass
 
 
-_cache: dict = {}
+# Plans made by fft / ifft / the autograd functions, least recently used
+# first.  Each holds a device allocation, so the cache is bounded: a workload
+# of ever new shapes (say, autograd over varying batch sizes) keeps at most
+# PLAN_CACHE_SIZE plans alive.
+PLAN_CACHE_SIZE = 64
+_cache: "collections.OrderedDict" = collections.OrderedDict()
 _cache_lock = threading.Lock()
+
+
+def _retire(p: Plan) -> None:
+    """Destroy an evicted plan once no kernel of it can still be running."""
+    torch.cuda.synchronize(p.device)
+    p.close()
 
 
 def get_plan(n: int, batch: int, inverse: bool, normalized: bool, device, dtype: str = "c64",
@@ -224,15 +247,23 @@ def get_plan(n: int, batch: int, inverse: bool, normalized: bool, device, dtype:
     key = (str(device), n, batch, inverse, normalized, dtype, scale_forward)
     with _cache_lock:
         p = _cache.get(key)
-        if p is None:
-            p = Plan(n, batch, inverse, dtype, normalized, device, scale_forward)
-            _cache[key] = p
+        if p is not None:
+            _cache.move_to_end(key)
+            return p
+        p = Plan(n, batch, inverse, dtype, normalized, device, scale_forward)
+        _cache[key] = p
+        while len(_cache) > PLAN_CACHE_SIZE:
+            _, old = _cache.popitem(last=False)
+            _retire(old)
         return p
 
 
 def clear_plan_cache():
     with _cache_lock:
+        plans = list(_cache.values())
         _cache.clear()
+    for p in plans:
+        _retire(p)
 
 
 def _run(x: torch.Tensor, inverse: bool, normalized: bool = True, dtype: str = "c64",

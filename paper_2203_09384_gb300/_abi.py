@@ -144,6 +144,10 @@ def lib() -> ctypes.CDLL:
     L.fft_plan_create_ragged.argtypes = [ctypes.POINTER(_i64), _i64, _int, _int, _u32, ctypes.POINTER(_vp)]
     L.fft_ragged_variant_count.restype = _int
     L.fft_ragged_variant_count.argtypes = []
+    L.fft_set_default_ragged_variant.restype = _int
+    L.fft_set_default_ragged_variant.argtypes = [_int]
+    L.fft_get_default_ragged_variant.restype = _int
+    L.fft_get_default_ragged_variant.argtypes = []
     L.fft_execute_noalloc.restype = _int
     L.fft_execute_noalloc.argtypes = [_i64, _i64, _int, _u32, _vp, _vp, _vp]
     L.fft_twiddle_fp32.restype = None
@@ -235,6 +239,14 @@ def fft_plan_create_ragged(offsets, direction: int = FFT_FORWARD, dtype: int = F
 
 def fft_ragged_variant_count() -> int:
     return lib().fft_ragged_variant_count()
+
+
+def fft_set_default_ragged_variant(variant: int) -> None:
+    check(lib().fft_set_default_ragged_variant(variant), "fft_set_default_ragged_variant")
+
+
+def fft_get_default_ragged_variant() -> int:
+    return lib().fft_get_default_ragged_variant()
 
 
 DTYPE_NAMES = {FFT_C64: "c64", FFT_C64_TC_F16: "tc_f16", FFT_C64_TC_BF16: "tc_bf16", FFT_C32: "c32"}

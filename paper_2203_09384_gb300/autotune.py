@@ -9,13 +9,16 @@ keeps the fastest, makes it the default through the C-ABI
 GPU name, library version and the compiled variant table, so later processes
 start from the tuned table (load_cache) without re-measuring.
 
-Cache location: $GBFFT_TUNE_CACHE, else ~/.cache/gbfft/tune.json.
+Cache location: $GBFFT_TUNE_CACHE, else ~/.cache/gbfft/tune.json.  The
+package applies it once per process, before its first plan (autoload), unless
+GBFFT_TUNE_CACHE is "off".
 """
 from __future__ import annotations
 
 import json
 import os
 import statistics
+import threading
 
 import torch
 
@@ -25,7 +28,10 @@ LENGTHS = [2 ** k for k in range(1, 12)]
 
 
 def cache_path() -> str:
-    return os.environ.get("GBFFT_TUNE_CACHE") or os.path.join(
+    env = os.environ.get("GBFFT_TUNE_CACHE")
+    if env and env.lower() != "off":
+        return env
+    return os.path.join(
         os.path.expanduser("~"), ".cache", "gbfft", "tune.json")
 
 
@@ -126,7 +132,9 @@ def save_cache(lengths_result: dict | None = None, ragged_result: dict | None = 
 
 
 def load_cache(path=None, device=None) -> dict:
-    """Apply a cached plain-length table (if any) for this GPU; returns it."""
+    """Apply the cached choices for this GPU, if any: the per-length FP32
+    defaults (fft_set_default_variant) and the ragged variant
+    (fft_set_default_ragged_variant); returns the cache entry."""
     path = path or cache_path()
     if not os.path.exists(path):
         return {}
@@ -140,4 +148,28 @@ def load_cache(path=None, device=None) -> dict:
         # only FP32 complex64 schedules can be a length's default
         if 0 <= v < _abi.fft_variant_count(n) and _abi.fft_variant_dtype(n, v) == _abi.FFT_C64:
             _abi.fft_set_default_variant(n, v)
+    rv = entry.get("ragged")
+    if isinstance(rv, int) and 0 <= rv < _abi.fft_ragged_variant_count():
+        _abi.fft_set_default_ragged_variant(rv)
     return entry
+
+
+_autoload_done = False
+_autoload_lock = threading.Lock()
+
+
+def autoload(device=None) -> None:
+    """Apply the tuning cache once per process, before the first plan is made
+    (Plan and RaggedPlan call this), so that tuning done by an earlier process
+    resumes.  GBFFT_TUNE_CACHE=off disables it."""
+    global _autoload_done
+    if _autoload_done:
+        return
+    with _autoload_lock:
+        if _autoload_done:
+            return
+        _autoload_done = True
+        if os.environ.get("GBFFT_TUNE_CACHE", "").lower() == "off":
+            return
+        if os.path.exists(cache_path()):
+            load_cache(device=device)

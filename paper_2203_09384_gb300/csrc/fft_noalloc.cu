@@ -53,9 +53,42 @@ struct DeviceState {
 DeviceState g_state[kMaxDevices];
 std::mutex g_mutex;
 
+// omega_m^k rounded to FP32 the way the plan path's host generator
+// (fft_twiddle_fp32) does it: k reduced to [0, m), the angle split into a
+// quadrant q (a factor (-i)^q, exact) and alpha in [0, pi/2), folded to
+// [0, pi/4] so that cos and sin see small arguments, FP64 cos/sin, then one
+// rounding to FP32.  The same steps on FP64 math give the same FP32 table as
+// the plan path (the tests compare the two paths' outputs bit for bit for
+// every compiled FP32 schedule).
+__device__ float2 noalloc_twiddle(long long m, long long k) {
+    k %= m;
+    if (k < 0) k += m;
+    const long long q = (4 * k) / m;
+    const long long r = 4 * k - q * m;
+    const double half_pi = 1.57079632679489661923;
+    double c, s;
+    if (2 * r <= m) {
+        const double a = half_pi * (double)r / (double)m;
+        c = cos(a);
+        s = sin(a);
+    } else {
+        const double b = half_pi * (double)(m - r) / (double)m;
+        c = sin(b);
+        s = cos(b);
+    }
+    double re, im;
+    switch (q) {
+        case 0: re = c; im = -s; break;
+        case 1: re = -s; im = -c; break;
+        case 2: re = -c; im = s; break;
+        default: re = s; im = c; break;
+    }
+    return make_float2((float)re, (float)im);
+}
+
 // Fill the first `count` twiddles of the schedule with radices r0..r3 (same
 // layout as the plan path's table: stage s >= 1, entry off_s + (r-1)*Ns + m =
-// omega_{Ns*R}^{m*r}) from FP64 sincospi, and clear the error word.
+// omega_{Ns*R}^{m*r}) and clear the error word.
 __global__ void noalloc_prepare(float2* scratch, int r0, int r1, int r2, int r3, int count) {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx == 0) *reinterpret_cast<int*>(scratch + kNoAllocTwiddles) = 0;
@@ -69,11 +102,7 @@ __global__ void noalloc_prepare(float2* scratch, int r0, int r1, int r2, int r3,
             const int local = idx - off;
             const int r = local / ns + 1;
             const int m = local % ns;
-            const long long M = (long long)ns * R;
-            const long long k = ((long long)m * r) % M;
-            double sn, cs;
-            sincospi(2.0 * (double)k / (double)M, &sn, &cs);
-            scratch[idx] = make_float2((float)cs, (float)(-sn));
+            scratch[idx] = noalloc_twiddle((long long)ns * R, (long long)m * r);
             return;
         }
         off += size;
@@ -142,6 +171,9 @@ fft_status_t kernel_shape(DeviceState* d, const gbfft::KernelEntry* e, int inver
 
 extern "C" fft_status_t fft_execute_noalloc(int64_t n, int64_t batch, int direction, uint32_t flags,
                                             const void* in, void* out, void* stream) {
+    // only the flags this call honours: normalisation and the schedule variant
+    if (flags & ~(uint32_t)(FFT_FLAG_UNNORMALIZED | FFT_FLAG_SCALE_FORWARD | FFT_FLAG_VARIANT_MASK))
+        return FFT_ERR_INVALID_VALUE;
     fft_status_t st = fft_validate(n, batch, direction, FFT_C64, flags);
     if (st != FFT_OK) return st;
     if (batch == 0) return FFT_OK;

@@ -6,15 +6,18 @@
 // re-shaped so that every length runs in a 256-thread block), and the tiles
 // become a device work list ordered from the longest length down.
 //
-// Five variants are compiled.  Bit 0 of variants 0..3 picks the schedule set:
-// set 0 keeps 16 complex elements per thread for N >= 32 (fewest exchanges),
-// set 1 keeps 8 (fewer registers, more resident blocks, finer tiles).  Bit 1
-// picks how blocks get work: 0 = a shared counter (one atomicAdd per item;
-// fft_execute clears it with a memset node first), 1 = static round robin with
-// the next item's descriptor prefetched.  Variant 4 runs set 1 with a bulk-copy
-// (TMA) ring that keeps the next item's signals in flight; variant 5 runs set
-// 0 in ring slots that a producer warp fills (exchanges inside the slot).
-// Every step is
+// Eight variants are compiled.  Bit 0 of variants 0..3 picks the schedule
+// set: set 0 keeps 16 complex elements per thread for N >= 32 (fewest
+// exchanges), set 1 keeps 8 (fewer registers, more resident blocks, finer
+// tiles).  Bit 1 picks how blocks get work: 0 = a shared counter (one
+// atomicAdd per item; fft_execute clears it with a memset node first), 1 =
+// static round robin with the next item's descriptor prefetched.  Variant 4
+// runs set 1 with a bulk-copy (TMA) ring that keeps the next item's signals in
+// flight.  Variants 5..7 run set 0 in ring slots that a producer warp fills
+// (exchanges inside the slot): 5 with 256 compute threads and 2 slots, 6 with
+// 128 compute threads and 2 slots (the default), 7 with 128 and 3 slots.
+// Variants 4..7 wait on mbarriers, with the same bounded waits, error word
+// and stall test mode as the uniform ring kernels.  Every step is
 // stream-ordered, so an execute can be captured in a CUDA graph.  The
 // autotuner picks a variant per workload.
 #include <cuda_runtime.h>
@@ -24,6 +27,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <new>
 #include <vector>
 
@@ -53,6 +57,7 @@ struct RaggedArgs {
     unsigned int* counter;
     int* err;          // device error word (bounded waits of the prefetch ring)
     uint64_t wait_ns;  // limit of each such wait
+    int stall;         // failure-detection test mode: the bulk-copy variants issue no copy
 };
 
 // per-variant, per-length schedules; every one has 256 threads per block
@@ -99,6 +104,9 @@ constexpr int kRaggedVariants = 8;
 constexpr int kRingVariant = 4;
 constexpr int kFirstProducerVariant = 5;
 constexpr int kDefaultRaggedVariant = 6;  // measured fastest on the mixed-length workload
+// the variant ragged plans use when the caller names none (process-wide; the
+// autotuner's cached choice is applied through fft_set_default_ragged_variant)
+std::atomic<int> g_default_ragged_variant{kDefaultRaggedVariant};
 __host__ __device__ constexpr bool is_producer_variant(int v) { return v >= kFirstProducerVariant; }
 
 // the ring variant's per-length schedules: set 1 with a 2-slot ring
@@ -286,7 +294,10 @@ __global__ void __launch_bounds__(kRaggedThreads, 3) fft_ragged_ring_kernel(Ragg
     }
     __syncthreads();
     RingInFlight inflight;  // thread 0's view of warp 0's copies in flight
-    if (tid < 32) {
+    // stall != 0 is the failure-detection test mode: nothing is issued, so the
+    // first wait of every block runs out, records FFT_ERR_TIMEOUT, and the
+    // block finishes its items without waiting or storing
+    if (tid < 32 && !a.stall) {
         for (int d = 0; d < 2; ++d) {
             const int it = (int)blockIdx.x + d * grid;
             if (it < a.n_items) {
@@ -432,6 +443,9 @@ __device__ __forceinline__ void slot_produce(const RaggedArgs& a, float2* ring, 
     constexpr int kSlotTile = SlotShape<NTC>::kTile;
     const int lane = threadIdx.x & 31;
     RingInFlight inflight;  // lane 0
+    // failure-detection test mode: copy nothing, so the compute threads' first
+    // wait runs out and they finish their items without waiting or storing
+    if (a.stall) return;
     int k = 0;
     for (int it = blockIdx.x; it < a.n_items; it += gridDim.x, ++k) {
         const int slot = k % kSlots;
@@ -639,12 +653,24 @@ struct RaggedState {
 
 int ragged_variant_count() { return kRaggedVariants; }
 
+bool ragged_set_default_variant(int v) {
+    if (v < 0 || v >= kRaggedVariants) return false;
+    g_default_ragged_variant.store(v);
+    return true;
+}
+
+int ragged_get_default_variant() { return g_default_ragged_variant.load(); }
+
+void ragged_set_wait_limit(RaggedState* st, uint64_t ns) { st->args.wait_ns = ns; }
+
+bool ragged_waits_on_device(const RaggedState* st) { return st->variant >= kRingVariant; }
+
 fft_status_t ragged_create(const int64_t* offsets, int64_t count, int direction, uint32_t flags,
                            RaggedState** out, int64_t* grid_out) {
     if (count < 0 || (count > 0 && !offsets)) return FFT_ERR_INVALID_VALUE;
     if (count > (int64_t)1 << 31) return FFT_ERR_INVALID_VALUE;
     int variant = (int)((flags & FFT_FLAG_VARIANT_MASK) >> 8) - 1;
-    if (variant < 0) variant = kDefaultRaggedVariant;
+    if (variant < 0) variant = g_default_ragged_variant.load();
     if (variant >= kRaggedVariants) return FFT_ERR_INVALID_VALUE;
     if (offsets && (offsets[0] < 0 || (offsets[0] & 1))) return FFT_ERR_MISALIGNED;
     std::vector<std::vector<int64_t>> buckets(GBFFT_MAX_LOG2N + 1);
@@ -725,6 +751,7 @@ fft_status_t ragged_create(const int64_t* offsets, int64_t count, int direction,
     st->args.scale_mode = st->scale_mode;
     st->args.err = reinterpret_cast<int*>(base + 16);
     st->args.wait_ns = 4000000000ull;
+    st->args.stall = (flags & FFT_FLAG_TEST_STALL) ? 1 : 0;
 
     // launch shape: persistent, every SM filled
     const void* k = ragged_kernel(variant, st->inverse);

@@ -566,14 +566,33 @@ cuda_fail:
 
 fft_status_t fft_plan_get_error(fft_plan_t p) {
     if (!p) return FFT_ERR_INVALID_VALUE;
-    if (!p->d_error) return cudaDeviceSynchronize() == cudaSuccess ? FFT_OK : FFT_ERR_CUDA;
-    int word = 0;
-    if (cudaMemcpy(&word, p->d_error, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return FFT_ERR_CUDA;
-    if (word != 0) {
-        const int zero = 0;
-        if (cudaMemcpy(p->d_error, &zero, sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess) return FFT_ERR_CUDA;
+    // Wait for every stream of the plan's device, non-blocking ones included
+    // (a plain cudaMemcpy would wait for the legacy stream only), then read
+    // and clear the word while no kernel of this device can be writing it.
+    int prev = -1;
+    if (cudaGetDevice(&prev) != cudaSuccess) {
+        cudaGetLastError();
+        return FFT_ERR_CUDA;
     }
-    return (fft_status_t)word;
+    fft_status_t st = FFT_OK;
+    if (prev != p->device && cudaSetDevice(p->device) != cudaSuccess) {
+        cudaGetLastError();
+        return FFT_ERR_CUDA;
+    }
+    int word = 0;
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+        st = FFT_ERR_CUDA;
+    } else if (p->d_error) {
+        if (cudaMemcpy(&word, p->d_error, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
+            st = FFT_ERR_CUDA;
+        } else if (word != 0) {
+            const int zero = 0;
+            if (cudaMemcpy(p->d_error, &zero, sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess) st = FFT_ERR_CUDA;
+        }
+    }
+    if (st != FFT_OK) cudaGetLastError();
+    if (prev != p->device) cudaSetDevice(prev);
+    return st != FFT_OK ? st : (fft_status_t)word;
 }
 
 fft_status_t fft_plan_destroy(fft_plan_t p) {
@@ -648,10 +667,20 @@ int fft_get_default_variant(int64_t n) {
 }
 
 fft_status_t fft_plan_set_wait_limit(fft_plan_t p, uint64_t nanoseconds) {
-    if (!p || nanoseconds == 0 || p->ragged) return FFT_ERR_INVALID_VALUE;
+    if (!p || nanoseconds == 0) return FFT_ERR_INVALID_VALUE;
+    if (p->ragged) {
+        gbfft::ragged_set_wait_limit(p->ragged, nanoseconds);
+        return FFT_OK;
+    }
     p->wait_ns = nanoseconds;
     return FFT_OK;
 }
+
+fft_status_t fft_set_default_ragged_variant(int variant) {
+    return gbfft::ragged_set_default_variant(variant) ? FFT_OK : FFT_ERR_INVALID_VALUE;
+}
+
+int fft_get_default_ragged_variant(void) { return gbfft::ragged_get_default_variant(); }
 
 fft_status_t fft_plan_get_twiddles(fft_plan_t p, void* host_out, int64_t count) {
     if (!p || (!host_out && count > 0) || p->ragged) return FFT_ERR_INVALID_VALUE;

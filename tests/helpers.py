@@ -1,6 +1,8 @@
 """Shared test helpers: error metrics and GPU runs through the C-ABI."""
 from __future__ import annotations
 
+import os
+
 import numpy as np
 import torch
 
@@ -88,3 +90,36 @@ def every_signal_violations(x: torch.Tensor, y: torch.Tensor, tol: float,
         bad.append(torch.nonzero(~ok).flatten() + r0)
         del xd, yd
     return torch.cat(bad).cpu() if bad else torch.empty(0, dtype=torch.int64)
+
+
+def oracle_max_rel_l2(x: torch.Tensor, y: torch.Tensor, inverse: bool = False, normalized: bool = True,
+                      rows=None, chunk_elems: int = 1 << 24, threads: int | None = None):
+    """Compare signals of y (a device or host tensor [batch, n], the library's
+    transform of x) element by element with the FP64 oracle's transform of
+    the same FP32 inputs, a chunk of signals at a time so host memory stays
+    bounded.  ``rows`` selects the signals (an index array; None = every
+    signal of the batch).  Returns (largest per-signal relative L2 error,
+    index of the signal that has it)."""
+    import oracle
+
+    batch, n = x.shape
+    threads = threads or os.cpu_count() or 1
+    step = max(1, chunk_elems // n)
+    worst, where = 0.0, -1
+    if rows is None:
+        chunks = ((r0, None) for r0 in range(0, batch, step))
+    else:
+        rows = np.asarray(rows, dtype=np.int64)
+        chunks = ((k, rows[k:k + step]) for k in range(0, rows.size, step))
+    for k, idx in chunks:
+        if idx is None:
+            xs, ys, base = x[k:k + step], y[k:k + step], np.arange(k, min(k + step, batch))
+        else:
+            ti = torch.from_numpy(idx).to(x.device)
+            xs, ys, base = x.index_select(0, ti), y.index_select(0, ti.to(y.device)), idx
+        want = oracle.reference(xs.cpu().numpy(), inverse, normalized, threads=threads)
+        e = rel_l2_per_signal(ys.cpu().numpy(), want)
+        i = int(e.argmax())
+        if e[i] > worst:
+            worst, where = float(e[i]), int(base[i])
+    return worst, where

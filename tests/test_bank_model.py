@@ -13,9 +13,9 @@ model follows the rows that are compiled.
 
 Measured factors it must reproduce (ncu
 ``l1tex__data_pipe_lsu_wavefronts_mem_shared`` over the same count minus
-``l1tex__data_bank_conflicts_pipe_lsu_mem_shared``, profiles
-fft_small_N32_2e25.md and fft_stockham_N64_2e25.md): the N = 32 one-thread-
-per-signal kernel 1.51x and the N = 64 direct kernel 1.50x, kernels whose
+``l1tex__data_bank_conflicts_pipe_lsu_mem_shared``, one 2^25-element launch
+of each kernel): the N = 32 one-thread-per-signal kernel 1.51x and the N = 64
+direct kernel 1.50x, kernels whose
 only shared-memory traffic is what the model replays.  The ring kernels also
 poll mbarriers from every lane and the issuing thread updates them, which the
 model leaves out: ncu counts about 1.25M extra wavefronts per 2^25 elements

@@ -31,3 +31,35 @@ def test_plans_need_a_cuda_device():
     with pytest.raises(ValueError):
         gb._cuda_device("cpu")
     assert gb._cuda_device("cuda:3") == torch.device("cuda", 3)
+
+
+def test_plan_cache_is_a_bounded_lru(monkeypatch):
+    """get_plan keeps at most PLAN_CACHE_SIZE plans: the least recently used
+    one is retired (its device synchronised, then the plan closed) when a new
+    shape comes in; a hit moves a plan to the most recent end."""
+    made, retired = [], []
+
+    class FakePlan:
+        def __init__(self, n, batch, *a, **k):
+            self.key = (n, batch)
+            made.append(self.key)
+
+        def close(self):
+            retired.append(self.key)
+
+    monkeypatch.setattr(gb, "Plan", FakePlan)
+    monkeypatch.setattr(gb, "_retire", lambda p: p.close())
+    monkeypatch.setattr(gb, "PLAN_CACHE_SIZE", 3)
+    monkeypatch.setattr(gb, "_cache", gb.collections.OrderedDict())
+    get = lambda b: gb.get_plan(64, b, False, True, "cuda:0")  # noqa: E731
+    a = get(1)
+    get(2)
+    get(3)
+    assert get(1) is a and made == [(64, 1), (64, 2), (64, 3)]  # a hit makes no plan
+    get(4)  # evicts batch 2, the least recently used
+    assert retired == [(64, 2)] and len(gb._cache) == 3
+    get(5)
+    assert retired == [(64, 2), (64, 3)]
+    assert get(1) is a
+    gb.clear_plan_cache()
+    assert sorted(retired) == sorted([(64, 1), (64, 2), (64, 3), (64, 4), (64, 5)]) and not gb._cache

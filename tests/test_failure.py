@@ -1,8 +1,8 @@
 """Failure detection without a GPU fault: bounded device-side waits.
 
 The test-only plan flag FFT_FLAG_TEST_STALL makes the kernels that wait on the
-device (the bulk-copy prefetch ring, the tensor-core MMA completion) issue
-nothing, so each wait runs out after the plan's wait limit (1 ms here), the
+device (the bulk-copy prefetch rings, ragged variants 4..7, the tensor-core MMA
+completion) issue nothing, so each wait runs out after the plan's wait limit (1 ms here), the
 kernel records FFT_ERR_TIMEOUT in the plan's error word and finishes.  The
 context must stay usable afterwards.
 """
@@ -51,6 +51,69 @@ def test_bounded_wait_reports_timeout(n, dtype, variant):
     tol = FP32_TOL if dtype == "c64" else 5e-3
     assert max_rel_l2(to_np(y[:64]), oracle.reference(x[:64].cpu().numpy())) <= tol
     good.close()
+
+
+def test_error_word_is_read_after_work_on_a_non_blocking_stream():
+    """fft_plan_get_error synchronises the plan's device, so a stalled kernel
+    enqueued on a non-blocking side stream has finished (and recorded its
+    timeout) before the word is read; the caller does no sync of its own."""
+    n, batch = 2048, 2 * 152 + 1
+    x = synth.uniform(batch, n, seed=3).cuda()
+    out = torch.zeros_like(x)
+    plan = gb.Plan(n, batch, extra_flags=gb.FFT_FLAG_TEST_STALL)
+    plan.set_wait_limit(50_000_000)  # 50 ms: still running when the host asks
+    side = torch.cuda.Stream()  # created cudaStreamNonBlocking
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        plan.execute(x, out, stream=side)
+    assert plan.error() == TIMEOUT
+    assert plan.error() == 0
+    assert torch.count_nonzero(out) == 0
+    plan.close()
+
+
+def _ragged_offsets():
+    lengths = synth.ragged_lengths(3000, seed=13)
+    return synth.ragged_offsets(lengths).numpy()
+
+
+@pytest.mark.parametrize("variant", [4, 5, 6, 7])
+def test_ragged_bounded_wait_reports_timeout(variant):
+    """The ragged variants that wait on the device (the bulk-copy ring, the
+    producer warp's ring slots): under the test flag nothing is copied, each
+    block's first wait runs out after the plan's 1 ms limit, the word reads
+    FFT_ERR_TIMEOUT once, nothing is stored, and the context stays usable."""
+    offsets = _ragged_offsets()
+    total = int(offsets[-1])
+    x = synth.uniform(1, total, seed=5).reshape(-1).cuda()
+    out = torch.zeros_like(x)
+    plan = gb.RaggedPlan(offsets, variant=variant, extra_flags=gb.FFT_FLAG_TEST_STALL)
+    plan.set_wait_limit(1_000_000)
+    plan.execute(x, out)
+    assert plan.error() == TIMEOUT
+    assert plan.error() == 0
+    assert torch.count_nonzero(out) == 0
+    plan.close()
+    good = gb.RaggedPlan(offsets, variant=variant)
+    y = good.execute(x)
+    assert good.error() == 0
+    first = slice(int(offsets[0]), int(offsets[1]))
+    want = oracle.reference(x[first].cpu().numpy()[None])
+    assert max_rel_l2(to_np(y[first])[None], want) <= FP32_TOL
+    good.close()
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+def test_ragged_variants_without_waits_ignore_the_test_flag(variant):
+    offsets = _ragged_offsets()[:201]
+    x = synth.uniform(1, int(offsets[-1]), seed=6).reshape(-1).cuda()
+    plan = gb.RaggedPlan(offsets, variant=variant, extra_flags=gb.FFT_FLAG_TEST_STALL)
+    plan.set_wait_limit(1_000_000)
+    y = plan.execute(x)
+    assert plan.error() == 0
+    first = slice(int(offsets[0]), int(offsets[1]))
+    assert max_rel_l2(to_np(y[first])[None], oracle.reference(x[first].cpu().numpy()[None])) <= FP32_TOL
+    plan.close()
 
 
 def test_kernels_without_waits_ignore_the_test_flag():

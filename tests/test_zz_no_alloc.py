@@ -3,7 +3,10 @@ memory (for example a process whose caching allocator owns all free device
 memory, or code that must not take the device-wide stall cudaMalloc/cudaFree
 can cause).  Its scratch is a static device array shared by all calls, so
 these checks run two calls in a row, with different lengths in between, and
-compare each result with the planned path (fft_plan_create + fft_execute).
+compare each result with the planned path (fft_plan_create + fft_execute):
+bit for bit, since both generate the same FP32 twiddle table by the same
+steps and run the same kernel, and with the FP64 oracle within the FP32
+tolerance.
 
 This file is named to be collected last; it also passes on its own in a fresh
 process (``pytest tests/test_zz_no_alloc.py -m gpu``).
@@ -12,6 +15,7 @@ import numpy as np
 import pytest
 import torch
 
+import oracle
 import synth
 from tests.helpers import FP32_TOL, max_rel_l2, to_np
 
@@ -52,14 +56,42 @@ def noalloc(x, n, batch, direction, flags):
 
 def test_matches_planned_path_on_two_calls_in_a_row():
     inputs = {c: synth.uniform(c[1], c[0], seed=31 + i).cuda() for i, c in enumerate(CASES)}
-    refs = {c: to_np(planned(inputs[c], *c)) for c in CASES}
+    refs = {c: planned(inputs[c], *c) for c in CASES}
     for c in CASES:  # consecutive calls alternate lengths, so the array is rewritten each time
         first = noalloc(inputs[c], *c)
         second = noalloc(inputs[c], *c)
         torch.cuda.synchronize()
+        n, batch, direction, flags = c
+        inverse = direction == _abi.FFT_INVERSE
+        normalized = not (flags & _abi.FFT_FLAG_UNNORMALIZED)
+        want = oracle.reference(inputs[c].cpu().numpy(), inverse, normalized, threads=8)
+        if flags & _abi.FFT_FLAG_SCALE_FORWARD:
+            want = want / n
         for got in (first, second):
-            err = max_rel_l2(to_np(got), refs[c])
+            assert torch.equal(got, refs[c]), c  # bit for bit
+            err = max_rel_l2(to_np(got), want)
             assert err <= FP32_TOL, (c, err)
+
+
+def _fp32_variants():
+    return [(n, v) for n in [2 ** k for k in range(1, 12)] for v in range(_abi.fft_variant_count(n))
+            if _abi.fft_variant_dtype(n, v) == _abi.FFT_C64]
+
+
+@pytest.mark.parametrize("n,variant", _fp32_variants())
+def test_every_fp32_schedule_bit_identical_to_planned(n, variant):
+    """Every compiled FP32 schedule through FFT_FLAG_VARIANT(k): its twiddle
+    table (written into the static array by this call) and its result equal
+    the planned path's bit for bit, forward and inverse, twice in a row."""
+    batch = 3 * 152 + 5
+    x = synth.uniform(batch, n, seed=50 + variant).cuda()
+    flags = _abi.FFT_FLAG_VARIANT(variant)
+    for direction in (_abi.FFT_FORWARD, _abi.FFT_INVERSE):
+        ref = planned(x, n, batch, direction, flags)
+        for _ in range(2):
+            got = noalloc(x, n, batch, direction, flags)
+            torch.cuda.synchronize()
+            assert torch.equal(got, ref), (n, variant, direction)
 
 
 def test_allocates_no_device_memory():
@@ -93,6 +125,12 @@ def test_rejects_bad_requests():
     assert L.fft_execute_noalloc(8, 4, 0, 0, p, p + 16, None) == code["FFT_ERR_OVERLAP"]
     assert L.fft_execute_noalloc(8, 1, 0, _abi.FFT_FLAG_VARIANT(7), p, p, None) == \
         code["FFT_ERR_INVALID_VALUE"]
+    # flags this call does not honour are refused, not ignored
+    for bad in (_abi.FFT_FLAG_TEST_STALL, _abi.FFT_FLAG_HOST_STAGING, 1 << 5):
+        assert L.fft_execute_noalloc(8, 1, 0, bad, p, p, None) == code["FFT_ERR_INVALID_VALUE"]
+    tc = next(v for v in range(_abi.fft_variant_count(256))
+              if _abi.fft_variant_dtype(256, v) != _abi.FFT_C64)  # a tensor-core or complex32 schedule
+    assert L.fft_execute_noalloc(256, 1, 0, _abi.FFT_FLAG_VARIANT(tc), p, p, None) == code["FFT_ERR_INVALID_VALUE"]
     assert L.fft_execute_noalloc(8, 0, 0, 0, None, None, None) == code["FFT_OK"]
     assert L.fft_status_string(code["FFT_ERR_NOALLOC_LIMIT"])
     torch.cuda.synchronize()
