@@ -64,11 +64,12 @@ enum {
     /* With FFT_FORWARD: multiply by 1/N, giving (1/N) F, the adjoint of the
      * normalised inverse (used for the backward pass of an inverse). */
     FFT_FLAG_SCALE_FORWARD = 1u << 1,
-    /* Bits 8..11: 1 + the schedule variant to use (0 = the length's default,
-     * see fft_set_default_variant).  Build them with FFT_FLAG_VARIANT(k). */
-    FFT_FLAG_VARIANT_MASK = 0xFu << 8,
+    /* Bits 8..12: 1 + the schedule variant to use, k = 0..30 (0 = the
+     * length's default, see fft_set_default_variant).  Build them with
+     * FFT_FLAG_VARIANT(k). */
+    FFT_FLAG_VARIANT_MASK = 0x1Fu << 8,
     /* Test hook for failure detection: kernels with device-side waits (the
-     * bulk-copy rings, the tensor-core stages, ragged variants 4..7) issue
+     * bulk-copy rings, the tensor-core stages, ragged variants 4 and up) issue
      * nothing, so their bounded waits run out after the plan's wait limit and
      * fft_plan_get_error reports FFT_ERR_TIMEOUT.  The output is not written.
      * Plans of kernels without device-side waits ignore it. */
@@ -121,7 +122,8 @@ GBFFT_API fft_status_t fft_plan_create(int64_t n, int64_t batch, int direction, 
  * flags: FFT_FLAG_UNNORMALIZED, FFT_FLAG_SCALE_FORWARD, FFT_FLAG_TEST_STALL,
  * FFT_FLAG_VARIANT(k) with k < fft_ragged_variant_count() (without it: the
  * process-wide default of fft_set_default_ragged_variant, initially variant
- * 6, a producer warp filling ring slots for 128 compute threads per block).
+ * 8, a producer warp filling ring slots for 128 compute threads per block,
+ * five blocks per SM).
  * Errors: FFT_ERR_INVALID_SIZE (a length), FFT_ERR_INVALID_VALUE, FFT_ERR_MISALIGNED
  * (odd offsets_host[0]), FFT_ERR_ALLOC, FFT_ERR_CUDA, FFT_ERR_NO_DEVICE.
  */
@@ -257,7 +259,7 @@ GBFFT_API int fft_variant_dtype(int64_t n, int variant);
 
 /*
  * Wall-time limit for the device-side waits of this plan's kernels (the
- * bulk-copy prefetch rings, ragged variants 4..7 and the tensor-core MMA
+ * bulk-copy prefetch rings, ragged variants 4 and up and the tensor-core MMA
  * completion wait on mbarriers).  A wait that runs out records FFT_ERR_TIMEOUT in the plan's
  * error word (see fft_plan_get_error); the block then stops waiting and
  * issuing, skips its stores and finishes, after waiting once more (with the

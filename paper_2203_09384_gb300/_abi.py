@@ -21,7 +21,7 @@ FFT_C64_TC_BF16 = 2
 FFT_C32 = 3
 FFT_FLAG_UNNORMALIZED = 1 << 0
 FFT_FLAG_SCALE_FORWARD = 1 << 1
-FFT_FLAG_VARIANT_MASK = 0xF << 8
+FFT_FLAG_VARIANT_MASK = 0x1F << 8
 FFT_FLAG_TEST_STALL = 1 << 16
 FFT_FLAG_HOST_STAGING = 1 << 17
 

@@ -13,10 +13,11 @@
 // atomicAdd per item; fft_execute clears it with a memset node first), 1 =
 // static round robin with the next item's descriptor prefetched.  Variant 4
 // runs set 1 with a bulk-copy (TMA) ring that keeps the next item's signals in
-// flight.  Variants 5..7 run set 0 in ring slots that a producer warp fills
+// flight.  Variants 5..8 run set 0 in ring slots that a producer warp fills
 // (exchanges inside the slot): 5 with 256 compute threads and 2 slots, 6 with
-// 128 compute threads and 2 slots (the default), 7 with 128 and 3 slots.
-// Variants 4..7 wait on mbarriers, with the same bounded waits, error word
+// 128 compute threads and 2 slots, 7 with 128 and 3 slots, 8 (the default) as
+// 6 with registers capped at 80 so that 5 blocks fit per SM.
+// Variants 4..8 wait on mbarriers, with the same bounded waits, error word
 // and stall test mode as the uniform ring kernels.  Every step is
 // stream-ordered, so an execute can be captured in a CUDA graph.  The
 // autotuner picks a variant per workload.
@@ -40,9 +41,11 @@ namespace gbfft {
 
 struct RaggedItem {
     int log2n;
-    int count;  // signals in this tile (<= S of the length's schedule)
-    int first;  // index of the tile's first signal in the bucketed offset list
+    int count;     // signals in this tile (<= S of the length's schedule)
+    int first;     // index of the tile's first signal in the bucketed offset list
     int pad;
+    int64_t off0;  // element offset of that first signal (= sig_off[first]): a
+                   // single-signal tile needs no second, dependent load
 };
 
 struct RaggedArgs {
@@ -96,14 +99,15 @@ GBFFT_RCFG(1, 11, 8, 1, 4, 8, 8, 8)
 #undef GBFFT_RCFG
 
 // variants 0..3: bit 0 schedule set, bit 1 work distribution; variant 4: the
-// schedule set 1 shapes fed by a bulk-copy (TMA) prefetch ring; variants 5..7:
+// schedule set 1 shapes fed by a bulk-copy (TMA) prefetch ring; variants 5..8:
 // set 0 shapes in ring slots filled by a producer warp (5: 256 compute threads
 // and 2 slots; 6 / 7: 128 compute threads, half the signals per tile, 2 / 3
-// slots)
-constexpr int kRaggedVariants = 8;
+// slots, 4 resident blocks per SM; 8: as 6 with registers capped for 5
+// resident blocks per SM)
+constexpr int kRaggedVariants = 9;
 constexpr int kRingVariant = 4;
 constexpr int kFirstProducerVariant = 5;
-constexpr int kDefaultRaggedVariant = 6;  // measured fastest on the mixed-length workload
+constexpr int kDefaultRaggedVariant = 8;  // measured fastest on the mixed-length workload
 // the variant ragged plans use when the caller names none (process-wide; the
 // autotuner's cached choice is applied through fft_set_default_ragged_variant)
 std::atomic<int> g_default_ragged_variant{kDefaultRaggedVariant};
@@ -128,11 +132,11 @@ struct SlotCfg {
                      0, -1, 0>;
     static_assert(type::NT == NTC, "one tile per compute group");
 };
-template <int NTC>
+template <int NTC, int MINB>
 struct SlotShape {
     static constexpr int kTile = NTC * 16;        // complex elements per tile (S * N) at most
     static constexpr int kThreads = NTC + 32;     // compute threads + the producer warp
-    static constexpr int kMinBlocks = NTC == 256 ? 2 : 4;
+    static constexpr int kMinBlocks = MINB;       // resident blocks per SM asked of the compiler
 };
 template <int V>
 struct RaggedMinBlocks {
@@ -154,7 +158,7 @@ constexpr int ragged_smem_bytes() {
 template <class C>
 __device__ __forceinline__ int64_t ragged_offset(const RaggedArgs& a, const RaggedItem& w) {
     const int sl = threadIdx.x / C::T;
-    return sl < w.count ? a.sig_off[w.first + sl] : 0;
+    return sl < w.count ? (sl == 0 ? w.off0 : a.sig_off[w.first + sl]) : 0;
 }
 
 template <class C, bool INV>
@@ -250,7 +254,7 @@ __device__ __forceinline__ void ragged_issue(const RaggedArgs& a, float2* slot_b
     if (lane == 0) mbar_arrive_expect_tx(bar, (uint32_t)(w.count * n * 8));
     __syncwarp();
     for (int k = lane; k < w.count; k += 32)
-        bulk_copy_g2s(slot_base + k * n, a.in + a.sig_off[w.first + k], (uint32_t)(n * 8), bar);
+        bulk_copy_g2s(slot_base + k * n, a.in + (k == 0 ? w.off0 : a.sig_off[w.first + k]), (uint32_t)(n * 8), bar);
 }
 
 template <class C, bool INV>
@@ -358,27 +362,47 @@ __global__ void __launch_bounds__(kRaggedThreads, 3) fft_ragged_ring_kernel(Ragg
 // ---------------------------------------------------------------------------
 // Exchange barrier of one signal: its slot region is touched by its own T
 // threads only, so a signal within one warp needs a warp sync, and a signal
-// spanning warps syncs its T threads on named barrier 1 + (index of its first
-// warp); barrier 0 stays the block's.  Warps are not synchronised between
-// items, so one warp group may already run a later item (another length,
-// other signal boundaries) while another is still exchanging in an earlier
-// one.  A barrier must never see arrivals with two thread counts at once.
-// That holds because a block's items come longest first (the host sorts the
-// work list by length, and a block takes a subsequence of it), so T never
-// grows from one item to the next: a later signal that uses barrier b lies
-// inside the earlier signal that used b (both start at warp b - 1), whose
-// warps all had to complete their barriers before any of them moved on.
-// (Were T to grow, warps of a later, wider signal could arrive at b while an
-// earlier, narrower signal still used it.)
+// spanning warps syncs its T threads on a named barrier of its own; barrier 0
+// stays the block's.  Warps are not synchronised between items, so one warp
+// group may already run a later item (another length, other signal
+// boundaries) while another is still exchanging in an earlier one.  A barrier
+// must never see arrivals with two thread counts at once, so every signal
+// width T has its own range of barrier numbers: signal group g (warps
+// g*T/32 .. (g+1)*T/32 - 1) of width T uses bar_base(T) + g.  A number is then
+// only ever used by the same warps with the same count, whatever the order of
+// the items, and consecutive uses by those warps follow one another.
+//
+// The barrier number is an immediate (one branch per signal group of the
+// block), so the compiler reserves only the barriers a kernel can name (1..3
+// for 128 compute threads, 1..6 for 256).  A number held in a register would
+// reserve all 16, and the SM's barrier supply would then cap the resident
+// blocks below what registers and shared memory allow.
+template <int NT, int T>
+constexpr int bar_base() {
+    int base = 1;
+    for (int t = 64; t < T; t *= 2) base += NT / t;
+    return base;
+}
+
+template <int T, int BASE, int G, int NG>
+__device__ __forceinline__ void signal_bar(int g) {
+    if constexpr (G < NG) {
+        if (g == G) {
+            asm volatile("bar.sync %0, %1;" ::"n"(BASE + G), "n"(T) : "memory");
+        } else {
+            signal_bar<T, BASE, G + 1, NG>(g);
+        }
+    }
+}
+
 template <class C>
 __device__ __forceinline__ void slot_sync() {
     if constexpr (C::T <= 32) {
         __syncwarp();
     } else {
-        static_assert(C::T % 32 == 0 && C::NT <= 15 * 32, "whole warps; barriers 1..15");
+        static_assert(C::T % 32 == 0 && bar_base<C::NT, C::T>() + C::NT / C::T <= 16, "whole warps; barriers 1..15");
         constexpr int kWarps = C::T / 32;  // warps per signal
-        const int first_warp = ((int)threadIdx.x >> 5) & ~(kWarps - 1);
-        asm volatile("bar.sync %0, %1;" ::"r"(1 + first_warp), "n"(C::T) : "memory");
+        signal_bar<C::T, bar_base<C::NT, C::T>(), 0, C::NT / C::T>(((int)threadIdx.x >> 5) / kWarps);
     }
 }
 
@@ -415,9 +439,11 @@ __device__ __forceinline__ void slot_tile(const RaggedArgs& a, const RaggedItem&
     twist_and_dft<C, 0>(v, t, tw, tc);
     slot_stages<C, 1>(v, slot, sl * C::N, t, tw, tc);
     // this thread is done with the slot: order its shared-memory accesses
-    // before the producer's next bulk copy into it, then release
+    // before the producer's next copy into it; once the whole warp is, one
+    // lane releases the slot for the warp (the barrier counts warps)
     fence_proxy_async_smem();
-    mbar_arrive(empty);
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) mbar_arrive(empty);
     store_last<C, INV>(v, a.out + off, t, active, scale);
 }
 
@@ -434,21 +460,29 @@ __device__ __forceinline__ int64_t slot_offset_for(const RaggedArgs& a, const Ra
 }
 
 // The producer warp.  Lane 0 sets each fill's byte count; every lane copies
-// signals lane, lane + 32, ...  Before it exits, lane 0 waits (bounded) for
-// the copies it issued last, so none lands after the block is gone even when
-// the compute threads gave up.
-template <int NTC, int SLOTS>
+// signals lane, lane + 32, ...  The next item's descriptor is loaded before
+// the wait for a free slot, so its latency hides behind that wait, and a
+// tile's first signal comes with its own offset (RaggedItem::off0), so a
+// single-signal tile costs one global load before its copy, not two.  Before
+// it exits, lane 0 waits (bounded) for the copies it issued last, so none
+// lands after the block is gone even when the compute threads gave up.
+template <int NTC, int SLOTS, int MINB>
 __device__ __forceinline__ void slot_produce(const RaggedArgs& a, float2* ring, uint64_t* full, uint64_t* empty) {
     constexpr int kSlots = SLOTS;
-    constexpr int kSlotTile = SlotShape<NTC>::kTile;
+    constexpr int kSlotTile = SlotShape<NTC, MINB>::kTile;
     const int lane = threadIdx.x & 31;
     RingInFlight inflight;  // lane 0
     // failure-detection test mode: copy nothing, so the compute threads' first
     // wait runs out and they finish their items without waiting or storing
     if (a.stall) return;
-    int k = 0;
-    for (int it = blockIdx.x; it < a.n_items; it += gridDim.x, ++k) {
+    int it = blockIdx.x;
+    if (it >= a.n_items) return;
+    RaggedItem w = a.items[it];
+    for (int k = 0;; ++k) {
         const int slot = k % kSlots;
+        const int nx = it + (int)gridDim.x;
+        RaggedItem wn{};
+        if (nx < a.n_items) wn = a.items[nx];  // in flight during the wait below
         if (k >= kSlots) {  // the compute threads must have released the slot's previous item
             bool ok = true;
             if (lane == 0) {
@@ -458,7 +492,6 @@ __device__ __forceinline__ void slot_produce(const RaggedArgs& a, float2* ring, 
             }
             if (!__shfl_sync(0xffffffffu, ok, 0)) break;
         }
-        const RaggedItem w = a.items[it];
         const int n = 1 << w.log2n;
         float2* dst = ring + slot * kSlotTile;
         if (lane == 0) {
@@ -467,16 +500,21 @@ __device__ __forceinline__ void slot_produce(const RaggedArgs& a, float2* ring, 
         }
         __syncwarp();
         for (int j = lane; j < w.count; j += 32)
-            bulk_copy_g2s(dst + j * n, a.in + a.sig_off[w.first + j], (uint32_t)(n * 8), &full[slot]);
+            bulk_copy_g2s(dst + j * n, a.in + (j == 0 ? w.off0 : a.sig_off[w.first + j]), (uint32_t)(n * 8),
+                          &full[slot]);
+        if (nx >= a.n_items) break;
+        it = nx;
+        w = wn;
     }
     if (lane == 0) inflight.drain(full, a.wait_ns);
 }
 
-template <int NTC, int SLOTS, bool INV>
-__global__ void __launch_bounds__(SlotShape<NTC>::kThreads, SlotShape<NTC>::kMinBlocks)
-    fft_ragged_slot_kernel(RaggedArgs a) {
+// The body of the producer-warp kernels; the __global__ wrappers below differ
+// only in how they bound registers.
+template <int NTC, int SLOTS, int MINB, bool INV>
+__device__ __forceinline__ void ragged_slot_body(const RaggedArgs& a) {
     constexpr int kSlots = SLOTS;
-    constexpr int kSlotTile = SlotShape<NTC>::kTile;
+    constexpr int kSlotTile = SlotShape<NTC, MINB>::kTile;
     extern __shared__ __align__(16) float2 smem[];
     float2* ring = smem;  // kSlots slots of kSlotTile elements
     uint64_t* full = reinterpret_cast<uint64_t*>(ring + kSlots * kSlotTile);
@@ -486,13 +524,13 @@ __global__ void __launch_bounds__(SlotShape<NTC>::kThreads, SlotShape<NTC>::kMin
     if (tid == 0) {
         for (int d = 0; d < kSlots; ++d) {
             mbar_init(&full[d], 1);
-            mbar_init(&empty[d], NTC);
+            mbar_init(&empty[d], NTC / 32);
         }
         fence_mbar_init();
     }
     __syncthreads();  // the last barrier of all NTC + 32 threads
     if (tid >= NTC) {
-        slot_produce<NTC, SLOTS>(a, ring, full, empty);
+        slot_produce<NTC, SLOTS, MINB>(a, ring, full, empty);
         return;
     }
     int it = blockIdx.x;
@@ -528,6 +566,22 @@ __global__ void __launch_bounds__(SlotShape<NTC>::kThreads, SlotShape<NTC>::kMin
         w = wn;
         off = offn;
     }
+}
+
+// Residency asked as a minimum of MINB blocks per SM (the compiler then
+// picks the register budget).
+template <int NTC, int SLOTS, int MINB, bool INV>
+__global__ void __launch_bounds__(SlotShape<NTC, MINB>::kThreads, SlotShape<NTC, MINB>::kMinBlocks)
+    fft_ragged_slot_kernel(RaggedArgs a) {
+    ragged_slot_body<NTC, SLOTS, MINB, INV>(a);
+}
+
+// Registers capped at REGS per thread directly (80 leaves room for 5 blocks
+// of 160 threads per SM); the minimum-blocks form of the same budget left
+// the compiler at 72 registers with spills in the exchange loop.
+template <int NTC, int SLOTS, int REGS, bool INV>
+__global__ void __maxnreg__(REGS) fft_ragged_slot_kernel_capped(RaggedArgs a) {
+    ragged_slot_body<NTC, SLOTS, 5, INV>(a);
 }
 
 // ---------------------------------------------------------------------------
@@ -616,14 +670,17 @@ const void* ragged_kernel(int v, bool inv) {
         case 2: return RaggedHost<2>::kernel(inv);
         case 3: return RaggedHost<3>::kernel(inv);
         case 5:
-            return inv ? reinterpret_cast<const void*>(&fft_ragged_slot_kernel<256, 2, true>)
-                       : reinterpret_cast<const void*>(&fft_ragged_slot_kernel<256, 2, false>);
+            return inv ? reinterpret_cast<const void*>(&fft_ragged_slot_kernel<256, 2, 2, true>)
+                       : reinterpret_cast<const void*>(&fft_ragged_slot_kernel<256, 2, 2, false>);
         case 6:
-            return inv ? reinterpret_cast<const void*>(&fft_ragged_slot_kernel<128, 2, true>)
-                       : reinterpret_cast<const void*>(&fft_ragged_slot_kernel<128, 2, false>);
+            return inv ? reinterpret_cast<const void*>(&fft_ragged_slot_kernel<128, 2, 4, true>)
+                       : reinterpret_cast<const void*>(&fft_ragged_slot_kernel<128, 2, 4, false>);
         case 7:
-            return inv ? reinterpret_cast<const void*>(&fft_ragged_slot_kernel<128, 3, true>)
-                       : reinterpret_cast<const void*>(&fft_ragged_slot_kernel<128, 3, false>);
+            return inv ? reinterpret_cast<const void*>(&fft_ragged_slot_kernel<128, 3, 4, true>)
+                       : reinterpret_cast<const void*>(&fft_ragged_slot_kernel<128, 3, 4, false>);
+        case 8:
+            return inv ? reinterpret_cast<const void*>(&fft_ragged_slot_kernel_capped<128, 2, 80, true>)
+                       : reinterpret_cast<const void*>(&fft_ragged_slot_kernel_capped<128, 2, 80, false>);
         default:
             return inv ? reinterpret_cast<const void*>(&fft_ragged_ring_kernel<true>)
                        : reinterpret_cast<const void*>(&fft_ragged_ring_kernel<false>);
@@ -703,8 +760,9 @@ fft_status_t ragged_create(const int64_t* offsets, int64_t count, int direction,
         tw_off[L] = tw_total;
         tw_total += twiddle_count(variant, L);
         const int S = signals_per_tile(variant, L);
+        // a tile must fit the kernel
         if (S < 1 || (variant == kRingVariant && (int64_t)S << L > kRingTile) ||
-            (is_producer_variant(variant) && (int64_t)S << L > (int64_t)producer_group(variant) * 16)) {  // a tile must fit the kernel
+            (is_producer_variant(variant) && (int64_t)S << L > (int64_t)producer_group(variant) * 16)) {
             delete st;
             return FFT_ERR_UNSUPPORTED;
         }
@@ -714,6 +772,7 @@ fft_status_t ragged_create(const int64_t* offsets, int64_t count, int direction,
             it.count = (int)std::min<size_t>(S, buckets[L].size() - k);
             it.first = (int)(sig.size() + k);
             it.pad = 0;
+            it.off0 = buckets[L][k];
             items.push_back(it);
         }
         sig.insert(sig.end(), buckets[L].begin(), buckets[L].end());

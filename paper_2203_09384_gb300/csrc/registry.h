@@ -44,7 +44,7 @@ int ragged_variant_count();
 bool ragged_set_default_variant(int v);  // false when v is not a ragged variant
 int ragged_get_default_variant();
 void ragged_set_wait_limit(RaggedState* st, uint64_t ns);
-bool ragged_waits_on_device(const RaggedState* st);  // the bulk-copy variants (4..7)
+bool ragged_waits_on_device(const RaggedState* st);  // the bulk-copy variants (4 and up)
 fft_status_t ragged_create(const int64_t* offsets, int64_t count, int direction, uint32_t flags,
                            RaggedState** out, int64_t* grid_out);
 fft_status_t ragged_execute(RaggedState* st, const void* in, void* out, void* stream);

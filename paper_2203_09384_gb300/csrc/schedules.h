@@ -43,10 +43,14 @@
     GX(7, 3, 16, 32, 8, 16, 0, 0, 2, 0, 1, 0, 0) \
     GX(7, 4, 16, 32, 8, 16, 0, 0, 2, 0, 2, 0, 0) \
     GX(8, 0, 16, 16, 16, 16, 0, 0, 1, 0, 0, 0, 2) \
-    GX(8, 1, 16, 8, 16, 16, 0, 0, 3, 2, 1, 0, 0) \
-    GX(8, 2, 16, 8, 16, 16, 0, 0, 3, 2, 2, 0, 0) \
+    GX(8, 7, 16, 8, 16, 16, 0, 0, 3, 2, 1, 0, 0) \
+    GX(8, 8, 16, 8, 16, 16, 0, 0, 3, 2, 2, 0, 0) \
     GX(8, 3, 16, 16, 16, 16, 0, 0, 1, 0, 1, 0, 0) \
     GX(8, 4, 16, 16, 16, 16, 0, 0, 1, 0, 2, 0, 0) \
+    GX(8, 9, 16, 16, 16, 16, 0, 0, 1, 0, 1, 0, 2) \
+    GX(8, 10, 16, 16, 16, 16, 0, 0, 1, 0, 2, 0, 2) \
+    GX(8, 1, 16, 8, 16, 16, 0, 0, 3, 2, 1, 0, 2) \
+    GX(8, 2, 16, 8, 16, 16, 0, 0, 3, 2, 2, 0, 2) \
     GX(9, 0, 16, 8, 8, 8, 8, 0, 2, 0, 0, 0, 3) \
     GX(9, 1, 16, 8, 8, 8, 8, 0, 1, 0, 0, 0, 0) \
     GX(10, 0, 16, 2, 8, 16, 8, 0, 2, 2, 0, 0, 2) \
@@ -66,15 +70,17 @@
     GX(11, 1, 16, 1, 8, 16, 16, 0, 1, 0, 0, 0, 0) \
     GX(11, 2, 16, 1, 8, 16, 16, 0, 2, 3, 0, 0, 0) \
     GX(11, 3, 16, 2, 8, 16, 16, 0, 1, 2, 0, 0, 0) \
-    GX(11, 4, 16, 1, 8, 16, 16, 0, 5, 2, 1, -3, 0) \
-    GX(11, 5, 16, 1, 8, 16, 16, 0, 5, 2, 2, -3, 0) \
+    GX(11, 15, 16, 1, 8, 16, 16, 0, 5, 2, 1, -3, 0) \
+    GX(11, 16, 16, 1, 8, 16, 16, 0, 5, 2, 2, -3, 0) \
     GX(11, 6, 16, 1, 8, 16, 16, 0, 3, 2, 1, 0, 0) \
     GX(11, 7, 16, 1, 8, 16, 16, 0, 3, 2, 2, 0, 0) \
     GX(11, 10, 16, 1, 8, 16, 16, 0, 3, 2, 0, 0, 2) \
     GX(11, 11, 16, 1, 8, 16, 16, 0, 5, 2, 1, -2, 0) \
     GX(11, 12, 16, 1, 8, 16, 16, 0, 5, 2, 2, -2, 0) \
     GX(11, 13, 16, 1, 8, 16, 16, 0, 4, 2, 1, 1, 0) \
-    GX(11, 14, 16, 1, 8, 16, 16, 0, 4, 2, 2, 1, 0)
+    GX(11, 14, 16, 1, 8, 16, 16, 0, 4, 2, 2, 1, 0) \
+    GX(11, 4, 16, 1, 8, 16, 16, 0, 5, 2, 1, -3, 2) \
+    GX(11, 5, 16, 1, 8, 16, 16, 0, 5, 2, 2, -3, 2)
 
 #define GBFFT_SMALL_SCHEDULES(SX) \
     SX(1, 0, 8, 1, 3)                \
@@ -124,4 +130,4 @@
 
 #define GBFFT_MIN_LOG2N 1
 #define GBFFT_MAX_LOG2N 11
-#define GBFFT_MAX_VARIANTS 15  // FFT_FLAG_VARIANT(k) holds k = 0..14
+#define GBFFT_MAX_VARIANTS 31  // FFT_FLAG_VARIANT(k) holds k = 0..30

@@ -122,3 +122,32 @@ def test_header_has_no_torch_types():
         text = f.read()
     assert "torch" not in text.lower().replace("pytorch", "") or "at::" not in text
     assert "at::Tensor" not in text and "c10" not in text
+
+
+def test_schedule_variant_numbers_are_unique():
+    """Every (length, variant) pair names ONE row across the four schedule
+    tables (FP32/tensor-core, one-thread-per-signal, complex32 and its
+    one-thread-per-signal form): a duplicate would silently replace a row in
+    the registry.  Each row's variant is in the flag's range, and the library
+    reports each row with the dtype of its own table."""
+    from tests.test_bank_model import _rows
+
+    seen = {}
+    tables = [("GBFFT_GENERIC_SCHEDULES", 13), ("GBFFT_SMALL_SCHEDULES", 5),
+              ("GBFFT_C32_SCHEDULES", 11), ("GBFFT_C32_SMALL_SCHEDULES", 5)]
+    for macro, nargs in tables:
+        rows = _rows(macro, nargs)
+        assert rows, macro
+        for row in rows:
+            key = (row[0], row[1])
+            assert key not in seen, f"variant {row[1]} of N=2^{row[0]} in {macro} and {seen.get(key)}"
+            seen[key] = macro
+            assert 0 <= row[1] <= 30
+            want = {"GBFFT_C32_SCHEDULES": _abi.FFT_C32, "GBFFT_C32_SMALL_SCHEDULES": _abi.FFT_C32,
+                    "GBFFT_SMALL_SCHEDULES": _abi.FFT_C64}.get(macro)
+            if want is None:  # generic rows: the TC column picks the dtype
+                want = [_abi.FFT_C64, _abi.FFT_C64_TC_F16, _abi.FFT_C64_TC_BF16][row[10]]
+            assert _abi.fft_variant_dtype(2 ** row[0], row[1]) == want, (macro, row)
+    for k in range(1, 12):
+        used = {v for (L, v) in seen if L == k}
+        assert _abi.fft_variant_count(2 ** k) == max(used) + 1
