@@ -221,9 +221,7 @@ def sample_stats(ms: list) -> dict:
 
 def tc_stage_count(info) -> int:
     """Radix-16 stages a plan runs on tensor cores (0 for an FP32 plan)."""
-    if info.tc == 0:
-        return 0
-    return sum(1 for s in range(info.num_stages) if info.radix[s] == 16)
+    return int(info.tc_stages)
 
 
 def _time_ms(fn, stream, reps: int = 10, warmup: int = 3, inner: int = 1) -> float:

@@ -237,6 +237,7 @@ typedef struct {
     int64_t grid;           /* blocks launched (persistent grid-stride loop)    */
     int64_t smem_bytes;     /* dynamic shared memory per block                  */
     int64_t twiddle_count;  /* complex64 entries in the plan's twiddle table    */
+    int tc_stages;          /* radix stages that run on tensor cores            */
 } fft_plan_info_t;
 
 GBFFT_API fft_status_t fft_plan_get_info(fft_plan_t plan, fft_plan_info_t* info);

@@ -79,6 +79,7 @@ class PlanInfo(ctypes.Structure):
         ("grid", ctypes.c_int64),
         ("smem_bytes", ctypes.c_int64),
         ("twiddle_count", ctypes.c_int64),
+        ("tc_stages", ctypes.c_int),
     ]
 
 

@@ -381,15 +381,20 @@ struct Cfg {
     static constexpr int kBuffers = kInRing ? 1 : XB_ ? XB_ : (kWarpLocal ? 1 : 2);
     static constexpr int kSmemElems = kInRing ? 0 : kBuffers * S * N;  // exchange buffers
     static constexpr int kRingElems = PIPE * S * N;               // prefetch ring
-    // 0: FP32 butterflies; 1 / 2: radix-16 stages on FP16 / BF16 tensor cores
-    static constexpr int TC = TC_;
+    // 0: FP32 butterflies; 1 / 2: radix-16 stages on FP16 / BF16 tensor cores;
+    // + 4: only the last radix-16 stage on tensor cores (one MMA round trip
+    // per tile), the others in FP32
+    static constexpr int TC = TC_ & 3;
+    static constexpr bool kTcLastOnly = (TC_ & 4) != 0;
+    static constexpr int kLast16 = R3 == 16 ? 3 : R2 == 16 ? 2 : R1 == 16 ? 1 : R0 == 16 ? 0 : -1;
     static constexpr int kTcTiles = NT / 128;  // 128-row MMA tiles per radix-16 stage
     // TMEM columns: FP32 accumulators (32 per tile), plus 16 for an A operand
     // kept in TMEM, rounded up to the allocation granularity
     static constexpr int kTcCols = kAInTmem ? 64 : 32 * kTcTiles;
     static constexpr int kTcACol = 32 * kTcTiles;  // first A column (kAInTmem)
     // radix-16 stages on the tensor cores
-    static constexpr int kTcStages = TC ? (R0 == 16) + (R1 == 16) + (R2 == 16) + (R3 == 16) : 0;
+    static constexpr int kTcStages =
+        !TC ? 0 : kTcLastOnly ? (kLast16 >= 0 ? 1 : 0) : (R0 == 16) + (R1 == 16) + (R2 == 16) + (R3 == 16);
     // FP16 dynamic range: a signal spanning warps is scaled once per tile by
     // its own power of two (measured faster there); a signal within one warp
     // scales each butterfly row before its conversion.  BF16: no scale.
@@ -403,6 +408,10 @@ struct Cfg {
     static constexpr int kSmemBytes = TC ? kTcOffset + kTcBytes : (kSmemElems + kRingElems) * 8 + 8 * PIPE;
     __host__ __device__ static constexpr int radix(int s) {
         return s == 0 ? R0 : s == 1 ? R1 : s == 2 ? R2 : R3;
+    }
+    // stage s runs on the tensor cores
+    __host__ __device__ static constexpr bool tc_stage(int s) {
+        return TC != 0 && E == 16 && radix(s) == 16 && (!kTcLastOnly || s == kLast16);
     }
     // Ns of stage s: product of the radices before it
     __host__ __device__ static constexpr int ns(int s) {
@@ -803,7 +812,7 @@ __device__ __forceinline__ void twist_and_dft(float2 (&v)[C::E], int t, const fl
 #pragma unroll
             for (int r = 1; r < R; ++r) v[c * R + r] = cmul(v[c * R + r], __ldg(twp + (r - 1) * Ns));
         }
-        if constexpr (C::TC != 0 && R == 16 && K == 1) {
+        if constexpr (C::tc_stage(s) && K == 1) {
             tc_dft16<C>(&v[0], tc);
         } else {
             Dft<R>::run(&v[c * R]);
@@ -1076,7 +1085,7 @@ template <class C, int s>
 __device__ __forceinline__ void rest_stages_in_ring(float2 (&v)[C::E], float2* b, int sb, int t,
                                                     const float2* __restrict__ tw, TcCtx& tc) {
     if constexpr (s < C::M) {
-        constexpr bool prev_tc = C::TC != 0 && C::radix(s - 1) == 16 && C::E == 16;
+        constexpr bool prev_tc = C::tc_stage(s - 1);
         if constexpr (!prev_tc) __syncthreads();
         scatter<C, s - 1>(v, b, sb, t);
         __syncthreads();

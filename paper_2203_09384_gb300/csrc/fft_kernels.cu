@@ -45,6 +45,7 @@ static KernelEntry generic_entry(int variant) {
     e.min_blocks = C::MINB;
     e.pipeline = C::PIPE;
     e.tc = C::TC;
+    e.tc_stages = C::kTcStages;
     e.tmem_cols = C::TC ? C::kTcCols : 0;
     e.twiddles = C::kTwiddles;
     if constexpr (C::kInRing) {

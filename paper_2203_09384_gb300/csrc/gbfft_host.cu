@@ -630,6 +630,7 @@ fft_status_t fft_plan_get_info(fft_plan_t p, fft_plan_info_t* info) {
     info->min_blocks = e->min_blocks;
     info->kernel_kind = (int)e->kind;
     info->tc = e->tc;
+    info->tc_stages = e->tc_stages;
     for (int s = 0; s < e->num_stages && s < 4; ++s) info->radix[s] = e->radix[s];
     info->grid = p->grid;
     info->smem_bytes = e->smem_bytes;

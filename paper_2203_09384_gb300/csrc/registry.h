@@ -26,6 +26,7 @@ struct KernelEntry {
     int min_blocks;          // launch-bounds hint
     int pipeline;            // bulk-copy ring depth (0 = none)
     int tc;                  // 0 FP32, 1 FP16 / 2 BF16 tensor-core radix-16 stages
+    int tc_stages;           // stages that run on the tensor cores
     int tmem_cols;           // TMEM columns one block allocates (tensor-core variants)
     int twiddles;            // complex64 entries in the twiddle table
     const void* kernel_fwd;

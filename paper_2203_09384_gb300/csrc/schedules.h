@@ -14,7 +14,8 @@
 //      TC = 0: FP32 butterflies; 1 / 2: every radix-16 stage runs as a dense
 //           16 x 16 complex product on FP16 / BF16 tensor cores (tcgen05),
 //           FP32 accumulation (FP16: a power-of-two prescale per butterfly
-//           row; BF16 shares FP32's exponent range and needs none),
+//           row; BF16 shares FP32's exponent range and needs none); 5 / 6:
+//           as 1 / 2 for the last radix-16 stage only,
 //      XB = exchange buffers: 0 = automatic, 1 = one buffer and two barriers
 //           per exchange (less shared memory, more resident blocks),
 //           -1 = none: with PIPE >= 2, every exchange reuses the ring slot
@@ -49,8 +50,10 @@
     GX(8, 4, 16, 16, 16, 16, 0, 0, 1, 0, 2, 0, 0) \
     GX(8, 9, 16, 16, 16, 16, 0, 0, 1, 0, 1, 0, 2) \
     GX(8, 10, 16, 16, 16, 16, 0, 0, 1, 0, 2, 0, 2) \
-    GX(8, 1, 16, 8, 16, 16, 0, 0, 3, 2, 1, 0, 2) \
+    GX(8, 11, 16, 8, 16, 16, 0, 0, 3, 2, 1, 0, 2) \
     GX(8, 2, 16, 8, 16, 16, 0, 0, 3, 2, 2, 0, 2) \
+    GX(8, 1, 16, 8, 16, 16, 0, 0, 3, 2, 5, 0, 2) \
+    GX(8, 12, 16, 8, 16, 16, 0, 0, 3, 2, 6, 0, 2) \
     GX(9, 0, 16, 8, 8, 8, 8, 0, 2, 0, 0, 0, 3) \
     GX(9, 1, 16, 8, 8, 8, 8, 0, 1, 0, 0, 0, 0) \
     GX(10, 0, 16, 2, 8, 16, 8, 0, 2, 2, 0, 0, 2) \
@@ -80,7 +83,9 @@
     GX(11, 13, 16, 1, 8, 16, 16, 0, 4, 2, 1, 1, 0) \
     GX(11, 14, 16, 1, 8, 16, 16, 0, 4, 2, 2, 1, 0) \
     GX(11, 4, 16, 1, 8, 16, 16, 0, 5, 2, 1, -3, 2) \
-    GX(11, 5, 16, 1, 8, 16, 16, 0, 5, 2, 2, -3, 2)
+    GX(11, 5, 16, 1, 8, 16, 16, 0, 5, 2, 2, -3, 2) \
+    GX(11, 17, 16, 1, 8, 16, 16, 0, 5, 2, 5, -3, 2) \
+    GX(11, 18, 16, 1, 8, 16, 16, 0, 5, 2, 6, -3, 2)
 
 #define GBFFT_SMALL_SCHEDULES(SX) \
     SX(1, 0, 8, 1, 3)                \

@@ -146,7 +146,7 @@ def test_schedule_variant_numbers_are_unique():
             want = {"GBFFT_C32_SCHEDULES": _abi.FFT_C32, "GBFFT_C32_SMALL_SCHEDULES": _abi.FFT_C32,
                     "GBFFT_SMALL_SCHEDULES": _abi.FFT_C64}.get(macro)
             if want is None:  # generic rows: the TC column picks the dtype
-                want = [_abi.FFT_C64, _abi.FFT_C64_TC_F16, _abi.FFT_C64_TC_BF16][row[10]]
+                want = [_abi.FFT_C64, _abi.FFT_C64_TC_F16, _abi.FFT_C64_TC_BF16][row[10] & 3]
             assert _abi.fft_variant_dtype(2 ** row[0], row[1]) == want, (macro, row)
     for k in range(1, 12):
         used = {v for (L, v) in seen if L == k}

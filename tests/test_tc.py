@@ -104,6 +104,17 @@ def _tc_variants():
     return out
 
 
+def _expected_tc_stages(n, variant):
+    """From the schedule table: TC & 4 puts only the last radix-16 stage on
+    the tensor cores, else every radix-16 stage."""
+    from tests.test_bank_model import _rows
+    for L, v, E, S, r0, r1, r2, r3, minb, pipe, tc, xb, ch in _rows("GBFFT_GENERIC_SCHEDULES", 13):
+        if 2 ** L == n and v == variant:
+            sixteen = [r for r in (r0, r1, r2, r3) if r == 16]
+            return (1 if sixteen else 0) if tc & 4 else len(sixteen)
+    raise KeyError((n, variant))
+
+
 @pytest.mark.parametrize("n,variant,dtype", _tc_variants())
 def test_every_tensor_core_schedule(n, variant, dtype):
     batch = 2 * 152 + 5
@@ -113,6 +124,7 @@ def test_every_tensor_core_schedule(n, variant, dtype):
         out = plan.execute(x.cuda())
         torch.cuda.synchronize()
         assert plan.error() == 0 and plan.info().variant == variant
+        assert plan.info().tc_stages == _expected_tc_stages(n, variant)
         plan.close()
         err = rel_l2_per_signal(to_np(out), oracle.reference(x.numpy(), inverse, threads=8))
         assert err.max() <= TC_TOL, (n, variant, dtype, inverse, err.max())
