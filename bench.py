@@ -511,7 +511,8 @@ def run_ours(args):
     if args.only_n:
         LOG2NS = [int(math.log2(int(v))) for v in args.only_n.split(",")]
     x = synth.uniform(1, ELEMS, seed=1 + rank, device=dev).reshape(-1)
-    plans = {k: gb.Plan(2 ** k, ELEMS // 2 ** k, device=dev, dtype=args.dtype) for k in LOG2NS}
+    variant = None if args.variant < 0 else args.variant
+    plans = {k: gb.Plan(2 ** k, ELEMS // 2 ** k, device=dev, dtype=args.dtype, variant=variant) for k in LOG2NS}
     c32 = args.dtype == "c32"
     if c32:
         # complex32 storage: the same U[-1, 1] values rounded to binary16, input
@@ -715,6 +716,8 @@ def main(argv=None):
                     help="comma list of the extra workloads to run (adjoint, ragged, precision)")
     ap.add_argument("--only-n", default="", help="comma list of lengths (profiling runs)")
     ap.add_argument("--elems", type=int, default=0, help="elements per length (profiling runs)")
+    ap.add_argument("--variant", type=int, default=-1,
+                    help="schedule variant of the length given by --only-n (profiling runs; default: the length's own)")
     ap.add_argument("--dtype", default="c64", choices=["c64", "tc_f16", "tc_bf16", "c32"],
                     help="arithmetic / storage of the sweep (runs of the tensor-core and complex32 paths)")
     ap.add_argument("--write-traffic", default="", metavar="NCU_CSV",
@@ -724,6 +727,8 @@ def main(argv=None):
     bad = [e for e in args.extras.split(",") if e and e not in EXTRAS]
     if bad:
         ap.error(f"unknown extras: {bad}")
+    if args.variant >= 0 and len([v for v in args.only_n.split(",") if v]) != 1:
+        ap.error("--variant needs exactly one length in --only-n")
     if args.write_traffic:
         write_traffic(args.write_traffic, args.elems or ELEMS)
         return 0

@@ -378,7 +378,11 @@ struct Cfg {
     // exchange buffers: one suffices when a signal stays in one warp; across
     // warps two let one barrier per exchange do (XB = 1 forces one buffer and
     // a second barrier, halving the shared memory of the exchange)
-    static constexpr int kBuffers = kInRing ? 1 : XB_ ? XB_ : (kWarpLocal ? 1 : 2);
+    // XB = 3: no shared memory at all; the one exchange of a two-stage
+    // schedule N = R x R with E = R (R lanes per signal) is an R x R transpose
+    // across those lanes done with warp shuffles (shuffle_transpose)
+    static constexpr bool kShuffle = XB_ == 3;
+    static constexpr int kBuffers = kInRing ? 1 : kShuffle ? 0 : XB_ ? XB_ : (kWarpLocal ? 1 : 2);
     static constexpr int kSmemElems = kInRing ? 0 : kBuffers * S * N;  // exchange buffers
     static constexpr int kRingElems = PIPE * S * N;               // prefetch ring
     // 0: FP32 butterflies; 1 / 2: radix-16 stages on FP16 / BF16 tensor cores;
@@ -434,6 +438,8 @@ struct Cfg {
     static_assert(32 % T == 0 || T % 32 == 0, "T must tile warps");
     static_assert(PIPE == 0 || PIPE >= 2, "the bulk-copy ring needs at least two slots");
     static_assert(!kInRing || PIPE >= 2, "exchanges in the ring slot need the bulk-copy ring");
+    static_assert(!kShuffle || (M == 2 && R0 == R1 && E == R0 && T == E && T <= 32 && PIPE == 0 && TC_ == 0),
+                  "shuffle exchange: two stages N = R x R, one butterfly of R per thread, R lanes per signal");
     static_assert(!kAInRing || TC == 0 || kTcTiles * 8192 <= S * N * 8, "the A operand must fit in a ring slot");
     static_assert(!kAInTmem || TC == 0 || kTcTiles == 1, "A in TMEM: one 128-row tile per block");
     // a signal spanning warps finds its maximum through shared memory after a
@@ -915,11 +921,48 @@ __device__ __forceinline__ void exchange_barrier() {
     }
 }
 
-// stages 1..M-1: exchange through shared memory, then butterflies
+// The exchange of a two-stage N = R x R schedule (kShuffle) by warp shuffles.
+// Thread t of a signal's R lanes holds row t of an R x R matrix (its stage-0
+// butterfly's outputs, v[q] = b_q of butterfly t) and needs column t (v[r] =
+// b_t of butterfly r, the Stockham read y[t + R r]).  For each lane bit b
+// (R/2 down to 1) the two lanes t and t ^ b swap the off-diagonal halves of
+// their 2b x 2b block: the lane with bit b clear keeps v[q] and sends v[q|b],
+// the lane with bit b set keeps v[q|b] and sends v[q], for every q with bit b
+// clear; after log2 R rounds every element sits at its transposed place.
+// Register indices are compile-time; the lane's choice is a select.
+template <class C>
+__device__ __forceinline__ void shuffle_transpose(float2 (&v)[C::E]) {
+    constexpr int R = C::E;
+    const int t = (int)threadIdx.x & (R - 1);  // R lanes per signal, aligned within the warp
+#pragma unroll
+    for (int b = R / 2; b >= 1; b >>= 1) {
+        const bool hi = (t & b) != 0;
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            if (q & b) continue;
+            const int q1 = q | b;
+            const float2 send = hi ? v[q] : v[q1];
+            float2 got;
+            got.x = __shfl_xor_sync(0xffffffffu, send.x, b);
+            got.y = __shfl_xor_sync(0xffffffffu, send.y, b);
+            if (hi) {
+                v[q] = got;
+            } else {
+                v[q1] = got;
+            }
+        }
+    }
+}
+
+// stages 1..M-1: exchange through shared memory (or, for kShuffle, warp
+// shuffles), then butterflies
 template <class C, int s>
 __device__ __forceinline__ void rest_stages(float2 (&v)[C::E], float2* smem, int& buf, int sb, int t,
                                             const float2* __restrict__ tw, TcCtx& tc) {
-    if constexpr (s < C::M) {
+    if constexpr (s < C::M && C::kShuffle) {
+        shuffle_transpose<C>(v);
+        twist_and_dft<C, s>(v, t, tw, tc);
+    } else if constexpr (s < C::M) {
         float2* b = smem + buf * (C::S * C::N);
         if constexpr (C::kBuffers == 1) {  // previous readers of b are done
             if constexpr (C::kWarpLocal) {

@@ -20,7 +20,9 @@
 //           per exchange (less shared memory, more resident blocks),
 //           -1 = none: with PIPE >= 2, every exchange reuses the ring slot
 //           the tile arrived in; -2 = as -1, and the tensor-core A operand
-//           lives in that slot too; -3 = as -1, with the A operand in TMEM,
+//           lives in that slot too; -3 = as -1, with the A operand in TMEM;
+//           3 = none: the exchange of a two-stage N = R x R row with E = R is
+//           a transpose by warp shuffles,
 //      CH = cache hints: bit 0 plain loads, bit 1 plain stores (else
 //           evict-first); the defaults are the measured best per length)
 // Threads per block = S * N / E.  Stage 0 with R0 = E/2 (and the last stage,
@@ -38,6 +40,8 @@
 #define GBFFT_GENERIC_SCHEDULES(GX)                   \
     GX(5, 1, 16, 128, 8, 4, 0, 0, 1, 0, 0, 0, 0) \
     GX(6, 0, 16, 64, 8, 8, 0, 0, 1, 0, 0, 0, 0) \
+    GX(6, 2, 8, 32, 8, 8, 0, 0, 1, 0, 0, 3, 0) \
+    GX(6, 3, 8, 32, 8, 8, 0, 0, 1, 0, 0, 0, 0) \
     GX(7, 0, 16, 32, 8, 16, 0, 0, 1, 0, 0, 0, 2) \
     GX(7, 1, 16, 16, 8, 16, 0, 0, 3, 2, 1, 0, 0) \
     GX(7, 2, 16, 16, 8, 16, 0, 0, 3, 2, 2, 0, 0) \
@@ -54,6 +58,7 @@
     GX(8, 2, 16, 8, 16, 16, 0, 0, 3, 2, 2, 0, 2) \
     GX(8, 1, 16, 8, 16, 16, 0, 0, 3, 2, 5, 0, 2) \
     GX(8, 12, 16, 8, 16, 16, 0, 0, 3, 2, 6, 0, 2) \
+    GX(8, 13, 16, 16, 16, 16, 0, 0, 1, 0, 0, 3, 2) \
     GX(9, 0, 16, 8, 8, 8, 8, 0, 2, 0, 0, 0, 3) \
     GX(9, 1, 16, 8, 8, 8, 8, 0, 1, 0, 0, 0, 0) \
     GX(10, 0, 16, 2, 8, 16, 8, 0, 2, 2, 0, 0, 2) \

@@ -172,7 +172,7 @@ def test_fp32_exchange_factors_stay_bounded():
     """No FP32 schedule row exchanges worse than 1.5x the conflict-free
     minimum (the worst: N = 32 and 64, both bound by HBM with these factors)."""
     for row in generic_rows():
-        if row["TC"]:
+        if row["TC"] or row["XB"] == 3:  # XB = 3 exchanges by warp shuffles, not shared memory
             continue
         f = generic_factor(row)
         assert f <= 1.5 + 1e-9, (row, f)

@@ -21,13 +21,44 @@ from tests.test_bank_model import _rows, swz8
 def all_rows():
     rows = []
     for L, v, E, S, r0, r1, r2, r3, minb, pipe, tc, xb, ch in _rows("GBFFT_GENERIC_SCHEDULES", 13):
-        rows.append(("GX", L, v, E, S, [r for r in (r0, r1, r2, r3) if r], pipe))
+        rows.append(("GX" if xb != 3 else "GX-shuffle", L, v, E, S, [r for r in (r0, r1, r2, r3) if r], pipe))
     for L, v, E, S, r0, r1, r2, r3, minb, pipe, xb in _rows("GBFFT_C32_SCHEDULES", 11):
         rows.append(("CX", L, v, E, S, [r for r in (r0, r1, r2, r3) if r], pipe))
     return rows
 
 
-def replay(N, E, S, radix, pipe, x, plant=None):
+def shuffle_transpose(v, plant=None):
+    """The kernels' shuffle_transpose on the registers of one signal's R
+    lanes: v[t, q] (lane t, register q) for an R x R tile.  For each lane bit
+    b, lanes t and t ^ b exchange: the lane with bit b clear sends v[q | b]
+    and keeps v[q], the other sends v[q] and keeps v[q | b] (q with bit b
+    clear).  Returns the registers after all rounds."""
+    R = v.shape[0]
+    v = v.copy()
+    b = R // 2
+    while b >= 1:
+        send = np.empty_like(v)
+        for t in range(R):
+            hi = bool(t & b) if plant != "lane-bit" else bool(t & (b >> 1 or R // 2))
+            for q in range(R):
+                if q & b:
+                    continue
+                send[t, q] = v[t, q] if hi else v[t, q | b]
+        for t in range(R):
+            hi = bool(t & b) if plant != "lane-bit" else bool(t & (b >> 1 or R // 2))
+            for q in range(R):
+                if q & b:
+                    continue
+                got = send[t ^ b, q]  # __shfl_xor_sync(send, b)
+                if hi:
+                    v[t, q] = got
+                else:
+                    v[t, q | b] = got
+        b //= 2
+    return v
+
+
+def replay(N, E, S, radix, pipe, x, plant=None, shuffle=False):
     """x: [S, N] complex; returns the tile's output [S, N] as the kernel
     computes it (exact arithmetic in complex128).  `plant` puts one plausible
     mistake into the mapping, to show the replay can fail."""
@@ -55,7 +86,12 @@ def replay(N, E, S, radix, pipe, x, plant=None):
                 v[tid, c * R + r] = flat[sb + j + r * stride]
     for s in range(M):
         R, K, Ns = radix[s], E // radix[s], ns(s)
-        if s > 0:
+        if s > 0 and shuffle:
+            # the warp-shuffle exchange of a two-stage R x R schedule
+            assert M == 2 and radix[0] == radix[1] == E == T
+            for g in range(NT // T):
+                v[g * T:(g + 1) * T] = shuffle_transpose(v[g * T:(g + 1) * T], plant)
+        elif s > 0:
             # exchange: scatter stage s-1's outputs, gather stage s's inputs
             Rp, Kp, Nsp = radix[s - 1], E // radix[s - 1], ns(s - 1)
             buf = {}
@@ -108,7 +144,7 @@ def test_schedule_row_computes_the_dft(row):
     assert int(np.prod(radix)) == N and all(E % r == 0 for r in radix)
     rng = np.random.default_rng(L * 100 + variant)
     x = rng.standard_normal((S, N)) + 1j * rng.standard_normal((S, N))
-    y = replay(N, E, S, radix, pipe, x)
+    y = replay(N, E, S, radix, pipe, x, shuffle=kind == "GX-shuffle")
     assert not np.isnan(y).any(), "an output element was never stored"
     assert np.allclose(y, np.fft.fft(x, axis=1), rtol=0, atol=1e-9 * N)
 
@@ -128,3 +164,15 @@ def test_replay_fails_on_a_planted_mistake(plant):
         except AssertionError:
             ok = False
         assert not ok, (plant, n)
+
+
+@pytest.mark.parametrize("R", [2, 4, 8, 16, 32])
+def test_shuffle_transpose_is_the_stockham_read(R):
+    """The shuffle rounds leave lane t holding column t (v[t, r] = in[r, t]),
+    which is the read y[t + R r] of the second stage; a lane bit taken from
+    the wrong round breaks it."""
+    rng = np.random.default_rng(R)
+    m = rng.standard_normal((R, R)) + 1j * rng.standard_normal((R, R))
+    assert np.array_equal(shuffle_transpose(m), m.T)
+    if R >= 4:
+        assert not np.array_equal(shuffle_transpose(m, plant="lane-bit"), m.T)
