@@ -91,7 +91,8 @@ typedef enum {
     FFT_ERR_CUDA = 6,          /* a CUDA runtime call or kernel launch failed */
     FFT_ERR_UNSUPPORTED = 7,   /* valid request this build cannot run         */
     FFT_ERR_TIMEOUT = 8,       /* a device-side bounded wait gave up          */
-    FFT_ERR_DEVICE_CHECK = 9,  /* a device-side consistency check failed      */
+    FFT_ERR_DEVICE_CHECK = 9,  /* a device-side bounds check of a GBFFT_DEBUG
+                                  build failed (release builds never set it)  */
     FFT_ERR_NO_DEVICE = 10,    /* no CUDA device, or not an sm_103 device     */
     FFT_ERR_NOALLOC_LIMIT = 11 /* fft_execute_noalloc: the request needs more
                                   scratch than its static array holds         */
@@ -205,7 +206,8 @@ GBFFT_API fft_status_t fft_execute_host(fft_plan_t plan, const void* in_host, vo
  * enqueued, and not while a stream of that device is being captured into a
  * CUDA graph.  Returns FFT_ERR_CUDA if the synchronisation or the copy fails
  * (for example after an earlier kernel fault), else the word: FFT_OK or the
- * code a kernel recorded (FFT_ERR_TIMEOUT).
+ * code a kernel recorded (FFT_ERR_TIMEOUT; in a GBFFT_DEBUG build also
+ * FFT_ERR_DEVICE_CHECK).
  */
 GBFFT_API fft_status_t fft_plan_get_error(fft_plan_t plan);
 

@@ -106,7 +106,13 @@ def lib() -> ctypes.CDLL:
         raise ImportError(
             f"libgbfft.so not built ({LIB_PATH} missing); run "
             "`python -c 'import __graft_entry__ as g; g.build()'` first")
-    L = ctypes.CDLL(LIB_PATH)
+    _lib = declare(ctypes.CDLL(LIB_PATH))
+    return _lib
+
+
+def declare(L: ctypes.CDLL) -> ctypes.CDLL:
+    """Give every C-ABI entry point of a loaded build its ctypes signature
+    (the package's own library, or the GBFFT_DEBUG build the tests load)."""
     L.fft_version.restype = ctypes.c_char_p
     L.fft_version.argtypes = []
     L.fft_status_string.restype = ctypes.c_char_p
@@ -153,7 +159,6 @@ def lib() -> ctypes.CDLL:
     L.fft_execute_noalloc.argtypes = [_i64, _i64, _int, _u32, _vp, _vp, _vp]
     L.fft_twiddle_fp32.restype = None
     L.fft_twiddle_fp32.argtypes = [_i64, _i64, ctypes.POINTER(ctypes.c_float)]
-    _lib = L
     return L
 
 

@@ -16,6 +16,9 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
+# GBFFT_DEBUG build (device-side bounds checks, NaN-poisoned exchanges): a
+# separate library for tests, never the one the package loads
+BUILD_DEBUG = os.path.join(HERE, "_build_debug")
 LIB = os.path.join(BUILD, "libgbfft.so")
 ROOT = os.path.dirname(HERE)
 INCLUDE = os.path.join(ROOT, "include")
@@ -51,11 +54,11 @@ def _stale(target, inputs):
     return any(os.path.getmtime(i) > t for i in inputs)
 
 
-def _compile(src, obj, defs, deps, verbose, build_dir=BUILD):
+def _compile(src, obj, defs, deps, verbose, build_dir=BUILD, extra=()):
     out = os.path.join(build_dir, "obj", obj)
     if not _stale(out, [src] + deps):
         return out, False
-    cmd = [nvcc(), *ARCH, *CFLAGS, "-I", os.path.dirname(src), *defs, "-c", src, "-o", out + ".tmp"]
+    cmd = [nvcc(), *ARCH, *CFLAGS, *extra, "-I", os.path.dirname(src), *defs, "-c", src, "-o", out + ".tmp"]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
     r = subprocess.run(cmd, capture_output=True, text=True)
@@ -68,9 +71,12 @@ def _compile(src, obj, defs, deps, verbose, build_dir=BUILD):
 
 
 def build(jobs: int | None = None, verbose: bool = False, force: bool = False,
-          csrc: str = CSRC, build_dir: str = BUILD) -> str:
+          csrc: str = CSRC, build_dir: str | None = None, debug: bool = False) -> str:
     """Compile every kernel unit of ``csrc`` and link ``<build_dir>/libgbfft.so``
-    (defaults: this package's sources into ``_build/``); returns its path."""
+    (defaults: this package's sources into ``_build/``, or with ``debug`` the
+    GBFFT_DEBUG build into ``_build_debug/``); returns its path."""
+    build_dir = build_dir or (BUILD_DEBUG if debug else BUILD)
+    extra = ("-DGBFFT_DEBUG",) if debug else ()
     lib_path = os.path.join(build_dir, "libgbfft.so")
     os.makedirs(os.path.join(build_dir, "obj"), exist_ok=True)
     units, deps = _sources(csrc)
@@ -81,7 +87,7 @@ def build(jobs: int | None = None, verbose: bool = False, force: bool = False,
                 os.remove(p)
     jobs = jobs or min(len(units), os.cpu_count() or 4)
     with cf.ThreadPoolExecutor(max_workers=jobs) as ex:
-        results = list(ex.map(lambda u: _compile(u[0], u[1], u[2], deps, verbose, build_dir), units))
+        results = list(ex.map(lambda u: _compile(u[0], u[1], u[2], deps, verbose, build_dir, extra), units))
     objs = [r[0] for r in results]
     if any(r[1] for r in results) or _stale(lib_path, objs):
         tmp = lib_path + f".tmp{os.getpid()}"
@@ -94,4 +100,4 @@ def build(jobs: int | None = None, verbose: bool = False, force: bool = False,
 
 
 if __name__ == "__main__":
-    print(build(verbose="-v" in sys.argv, force="--force" in sys.argv))
+    print(build(verbose="-v" in sys.argv, force="--force" in sys.argv, debug="--debug" in sys.argv))

@@ -322,6 +322,36 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 
 // status code written to the plan's error word by a wait that gave up
 constexpr int kErrTimeout = 8;
+// status code written by a failed device-side check of a GBFFT_DEBUG build
+constexpr int kErrDeviceCheck = 9;
+
+// ---------------------------------------------------------------------------
+// GBFFT_DEBUG builds (a separate library, for tests): every shared-memory
+// exchange index, stage-0 tile read, global element index and twiddle index
+// is checked against its buffer; a failed check records FFT_ERR_DEVICE_CHECK
+// in the plan's error word (first error wins) and the access is skipped, so
+// nothing faults.  And every exchange slot a thread reads is poisoned with NaN
+// right after the read: each slot is read once per stage, so a slot the next
+// scatter fails to write reaches the output as NaN.  The plan's error word
+// reaches the helpers through a block-wide pointer each kernel sets first.
+// Release builds compile all of this away.
+// ---------------------------------------------------------------------------
+#ifdef GBFFT_DEBUG
+__shared__ int* g_dbg_err;
+__device__ __forceinline__ void dbg_set_err(int* err) {
+    if (threadIdx.x == 0) g_dbg_err = err;
+    __syncthreads();
+}
+__device__ __forceinline__ bool dbg_ok(bool cond) {
+    if (!cond && g_dbg_err) atomicCAS(g_dbg_err, 0, kErrDeviceCheck);
+    return cond;
+}
+#define GBFFT_DBG_ONLY(...) __VA_ARGS__
+#else
+__device__ __forceinline__ void dbg_set_err(int*) {}
+__device__ __forceinline__ constexpr bool dbg_ok(bool) { return true; }
+#define GBFFT_DBG_ONLY(...)
+#endif
 
 // Bulk copies that thread 0 issued into ring slots and has not yet seen
 // complete (at most one per slot).  A block whose wait gave up stops waiting
@@ -816,7 +846,10 @@ __device__ __forceinline__ void twist_and_dft(float2 (&v)[C::E], int t, const fl
             const int j = bfly<C, s>(t, c);
             const float2* twp = tw + C::tw_off(s) + (j & (Ns - 1));
 #pragma unroll
-            for (int r = 1; r < R; ++r) v[c * R + r] = cmul(v[c * R + r], __ldg(twp + (r - 1) * Ns));
+            for (int r = 1; r < R; ++r) {
+                if (!dbg_ok(C::tw_off(s) + (j & (Ns - 1)) + (r - 1) * Ns < C::kTwiddles)) continue;
+                v[c * R + r] = cmul(v[c * R + r], __ldg(twp + (r - 1) * Ns));
+            }
         }
         if constexpr (C::tc_stage(s) && K == 1) {
             tc_dft16<C>(&v[0], tc);
@@ -837,13 +870,16 @@ __device__ __forceinline__ void scatter(const float2 (&v)[C::E], float2* buf, in
         const int j = bfly<C, s>(t, c);
         const int base = sb + (j / Ns) * (Ns * R) + (j & (Ns - 1));
 #pragma unroll
-        for (int q = 0; q < R; ++q) buf[swz8(base + q * Ns)] = v[c * R + q];
+        for (int q = 0; q < R; ++q) {
+            if (!dbg_ok(base + q * Ns >= 0 && base + q * Ns < C::S * C::N)) continue;
+            buf[swz8(base + q * Ns)] = v[c * R + q];
+        }
     }
 }
 
-// shared memory -> stage s inputs
+// shared memory -> stage s inputs (GBFFT_DEBUG: each slot poisoned once read)
 template <class C, int s>
-__device__ __forceinline__ void gather(float2 (&v)[C::E], const float2* buf, int sb, int t) {
+__device__ __forceinline__ void gather(float2 (&v)[C::E], float2* buf, int sb, int t) {
     constexpr int R = C::radix(s);
     constexpr int K = C::E / R;
     constexpr int stride = C::N / R;
@@ -851,7 +887,12 @@ __device__ __forceinline__ void gather(float2 (&v)[C::E], const float2* buf, int
     for (int c = 0; c < K; ++c) {
         const int j = bfly<C, s>(t, c);
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[c * R + r] = buf[swz8(sb + j + r * stride)];
+        for (int r = 0; r < R; ++r) {
+            const int a = sb + j + r * stride;
+            if (!dbg_ok(a >= 0 && a < C::S * C::N)) continue;
+            v[c * R + r] = buf[swz8(a)];
+            GBFFT_DBG_ONLY(buf[swz8(a)] = make_float2(__int_as_float(0x7fc00000), __int_as_float(0x7fc00000));)
+        }
     }
 }
 
@@ -871,6 +912,7 @@ __device__ __forceinline__ void load_first(float2 (&v)[C::E], const float2* src,
         for (int r = 0; r < R; ++r) {
 #pragma unroll
             for (int c = 0; c < K; c += 2) {
+                if (!dbg_ok(K * t + c + r * stride + 1 < C::N)) continue;
                 float4 f = ld_stream4<C::CH>(src + K * t + c + r * stride);
                 v[c * R + r] = make_float2(f.x, f.y);
                 v[(c + 1) * R + r] = make_float2(f.z, f.w);
@@ -878,7 +920,10 @@ __device__ __forceinline__ void load_first(float2 (&v)[C::E], const float2* src,
         }
     } else {
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[r] = ld_stream2<C::CH>(src + t + r * stride);
+        for (int r = 0; r < R; ++r) {
+            if (!dbg_ok(t + r * stride < C::N)) continue;
+            v[r] = ld_stream2<C::CH>(src + t + r * stride);
+        }
     }
     if constexpr (INV) {
 #pragma unroll
@@ -904,11 +949,17 @@ __device__ __forceinline__ void store_last(float2 (&v)[C::E], float2* dst, int t
 #pragma unroll
         for (int q = 0; q < R; ++q) {
 #pragma unroll
-            for (int c = 0; c < K; c += 2) st_stream4<C::CH>(dst + K * t + c + q * stride, v[c * R + q], v[(c + 1) * R + q]);
+            for (int c = 0; c < K; c += 2) {
+                if (!dbg_ok(K * t + c + q * stride + 1 < C::N)) continue;
+                st_stream4<C::CH>(dst + K * t + c + q * stride, v[c * R + q], v[(c + 1) * R + q]);
+            }
         }
     } else {
 #pragma unroll
-        for (int q = 0; q < R; ++q) st_stream2<C::CH>(dst + t + q * stride, v[q]);
+        for (int q = 0; q < R; ++q) {
+            if (!dbg_ok(t + q * stride < C::N)) continue;
+            st_stream2<C::CH>(dst + t + q * stride, v[q]);
+        }
     }
 }
 
@@ -991,6 +1042,7 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
     const int t = tid % C::T;
     const int sb = sl * C::N;
     const int64_t ntiles = (batch + C::S - 1) / C::S;
+    dbg_set_err(err);
     TcCtx tc;
     if constexpr (C::TC != 0) tc_setup<C>(tc, reinterpret_cast<unsigned char*>(smem) + C::kTcOffset, err, wait_ns);
     tc.stall = stall != 0;
@@ -1019,6 +1071,7 @@ __device__ __forceinline__ void gather_tile(float2 (&v)[C::E], const float2* til
         const int j = bfly<C, 0>(t, c);
 #pragma unroll
         for (int r = 0; r < R; ++r) {
+            if (!dbg_ok(sb + j + r * stride < C::S * C::N)) continue;
             float2 a = tile[sb + j + r * stride];
             v[c * R + r] = INV ? conj2(a) : a;
         }
@@ -1045,6 +1098,7 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
     const int t = tid % C::T;
     const int sb = sl * C::N;
     const int64_t ntiles = (batch + C::S - 1) / C::S;
+    dbg_set_err(err);
 
     RingInFlight inflight;  // thread 0's copies in flight
     // copy the tile of the block's iteration `j` into slot j mod D (thread 0 only)
@@ -1160,6 +1214,7 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
     const int t = tid % C::T;
     const int sb = sl * C::N;
     const int64_t ntiles = (batch + C::S - 1) / C::S;
+    dbg_set_err(err);
 
     RingInFlight inflight;  // thread 0's copies in flight
     // copy the tile of the block's iteration `j` into slot j mod D (thread 0 only)
@@ -1450,6 +1505,7 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
     const int sb = sl * C::N;
     const int ls = log2_pow2(scale);
     const int64_t ntiles = (batch + C::S - 1) / C::S;
+    dbg_set_err(err);
     TcCtx tc;  // FP32 butterflies only
     int buf = 0;
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
@@ -1505,6 +1561,7 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
     const int sb = sl * C::N;
     const int ls = log2_pow2(scale);
     const int64_t ntiles = (batch + C::S - 1) / C::S;
+    dbg_set_err(err);
 
     RingInFlight inflight;  // thread 0's copies in flight
     // copy the tile of the block's iteration `j` into slot j mod D (thread 0 only)

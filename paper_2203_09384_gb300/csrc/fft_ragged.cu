@@ -211,6 +211,7 @@ template <int V, bool INV>
 __global__ void __launch_bounds__(kRaggedThreads, RaggedMinBlocks<V & 1>::value) fft_ragged_kernel(RaggedArgs a) {
     constexpr int S = V & 1;  // schedule set
     extern __shared__ __align__(16) float2 smem[];
+    dbg_set_err(a.err);
     if constexpr ((V >> 1) == 0) {
         __shared__ int s_item;
         for (;;) {
@@ -291,6 +292,7 @@ __global__ void __launch_bounds__(kRaggedThreads, 3) fft_ragged_ring_kernel(Ragg
     uint64_t* bars = reinterpret_cast<uint64_t*>(ring + 2 * kRingTile);
     const int tid = threadIdx.x;
     const int grid = (int)gridDim.x;
+    dbg_set_err(a.err);
     if (tid == 0) {
         mbar_init(&bars[0], 1);
         mbar_init(&bars[1], 1);
@@ -521,6 +523,7 @@ __device__ __forceinline__ void ragged_slot_body(const RaggedArgs& a) {
     uint64_t* empty = full + kSlots;
     const int tid = threadIdx.x;
     const int grid = (int)gridDim.x;
+    dbg_set_err(a.err);
     if (tid == 0) {
         for (int d = 0; d < kSlots; ++d) {
             mbar_init(&full[d], 1);
