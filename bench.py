@@ -666,15 +666,12 @@ def run_ours(args):
     return 0
 
 
-def write_traffic(csv_path: str, elems: int, out_path: str | None = None) -> dict:
-    """Write profiles/traffic.json from an ncu CSV log of one forward launch per
-    length in sweep order (dram__bytes_read.sum and dram__bytes_write.sum),
-    scaled to the benchmark's 2^28 elements per launch when captured smaller,
-    with the hash of the kernel sources it describes."""
+def _csv_dram_bytes(csv_path: str) -> list:
+    """dram__bytes_read.sum + dram__bytes_write.sum of every launch in an ncu
+    CSV log, in launch order."""
     import csv
 
-    per_id = {}
-    order = []
+    per_id, order = {}, []
     with open(csv_path) as f:
         rows = [r for r in csv.reader(line for line in f if not line.startswith("=="))]
     hdr = rows[0]
@@ -688,13 +685,31 @@ def write_traffic(csv_path: str, elems: int, out_path: str | None = None) -> dic
             per_id[r[i_id]] = 0.0
             order.append(r[i_id])
         per_id[r[i_id]] += float(r[i_val].replace(",", "")) * scale[r[i_unit]]
-    if len(order) != len(LOG2NS):
-        raise SystemExit(f"expected {len(LOG2NS)} launches, found {len(order)}")
+    return [per_id[i] for i in order]
+
+
+def write_traffic(csv_paths: str, elems: int, out_path: str | None = None) -> dict:
+    """Write profiles/traffic.json from ncu CSV logs of DRAM bytes
+    (dram__bytes_read.sum and dram__bytes_write.sum): either one log per
+    length (comma-separated, sweep order, one launch each) or one log of one
+    sweep step (a launch per length).  Captured at `elems` elements per
+    launch and scaled to the benchmark's 2^28, with the hash of the kernel
+    sources it describes."""
+    paths = [p for p in csv_paths.split(",") if p]
+    launches = []
+    for p in paths:
+        got = _csv_dram_bytes(p)
+        launches.extend(got if len(paths) == 1 else got[:1])
+    if len(launches) != len(LOG2NS):
+        raise SystemExit(f"expected {len(LOG2NS)} launches, found {len(launches)}")
     factor = ELEMS / elems
+    note = "dram__bytes_read.sum + dram__bytes_write.sum of one forward launch per length"
+    if len(paths) > 1:
+        note += ", each length captured on its own"
+    if factor != 1:
+        note += f", times {factor:g} (traffic grows in proportion to the elements)"
     out = {"source_hash": kernel_source_hash(), "captured_elements": elems, "scaled_to_elements": ELEMS,
-           "note": "dram__bytes_read.sum + dram__bytes_write.sum of one forward launch per length"
-                   + (f", times {factor:g} (traffic grows in proportion to the elements)" if factor != 1 else ""),
-           "bytes_per_launch": {str(2 ** k): per_id[i] * factor for k, i in zip(LOG2NS, order)}}
+           "note": note, "bytes_per_launch": {str(2 ** k): b * factor for k, b in zip(LOG2NS, launches)}}
     with open(out_path or os.path.join(ROOT, "profiles", "traffic.json"), "w") as f:
         json.dump(out, f, indent=1)
         f.write("\n")
@@ -720,9 +735,9 @@ def main(argv=None):
                     help="schedule variant of the length given by --only-n (profiling runs; default: the length's own)")
     ap.add_argument("--dtype", default="c64", choices=["c64", "tc_f16", "tc_bf16", "c32"],
                     help="arithmetic / storage of the sweep (runs of the tensor-core and complex32 paths)")
-    ap.add_argument("--write-traffic", default="", metavar="NCU_CSV",
-                    help="write profiles/traffic.json from an ncu DRAM-bytes CSV of one sweep step "
-                         "(captured with --elems, if given) and exit")
+    ap.add_argument("--write-traffic", default="", metavar="NCU_CSV[,NCU_CSV...]",
+                    help="write profiles/traffic.json from ncu DRAM-bytes CSVs (one per length, or one of a "
+                         "whole sweep step; captured with --elems, if given) and exit")
     args = ap.parse_args(argv)
     bad = [e for e in args.extras.split(",") if e and e not in EXTRAS]
     if bad:

@@ -40,6 +40,22 @@ def test_write_traffic_sums_and_scales(tmp_path):
     assert bench.ncu_traffic(11, str(out_path)) is None
 
 
+def test_write_traffic_from_one_capture_per_length(tmp_path):
+    """One CSV per length (each length captured on its own, one launch each,
+    in sweep order): the same sums, in the order of the files."""
+    launches = [(100.0 + k, 90.0 + k) for k in range(len(bench.LOG2NS))]
+    paths = []
+    for k, launch in enumerate(launches):
+        p = tmp_path / f"n{k}.csv"
+        _ncu_csv(p, [launch])
+        paths.append(str(p))
+    out = bench.write_traffic(",".join(paths), bench.ELEMS // 8, str(tmp_path / "traffic.json"))
+    for k, (rd, wr) in zip(bench.LOG2NS, launches):
+        got = out["bytes_per_launch"][str(2 ** k)]
+        assert abs(got - 8 * (rd + wr) * 1e6) <= 1e-6 * got
+    assert "on its own" in out["note"]
+
+
 def test_write_traffic_rejects_a_short_capture(tmp_path):
     csv_path = tmp_path / "t.csv"
     _ncu_csv(csv_path, [(1.0, 1.0)] * 3)
