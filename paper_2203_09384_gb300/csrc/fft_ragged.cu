@@ -16,8 +16,9 @@
 // flight.  Variants 5..8 run set 0 in ring slots that a producer warp fills
 // (exchanges inside the slot): 5 with 256 compute threads and 2 slots, 6 with
 // 128 compute threads and 2 slots, 7 with 128 and 3 slots, 8 (the default) as
-// 6 with registers capped at 80 so that 5 blocks fit per SM.
-// Variants 4..8 wait on mbarriers, with the same bounded waits, error word
+// 6 with registers capped at 80 so that 5 blocks fit per SM, 9 the kernel of 8
+// with the lengths up to 64 first in the work list.
+// Variants 4..9 wait on mbarriers, with the same bounded waits, error word
 // and stall test mode as the uniform ring kernels.  Every step is
 // stream-ordered, so an execute can be captured in a CUDA graph.  The
 // autotuner picks a variant per workload.
@@ -103,11 +104,13 @@ GBFFT_RCFG(1, 11, 8, 1, 4, 8, 8, 8)
 // set 0 shapes in ring slots filled by a producer warp (5: 256 compute threads
 // and 2 slots; 6 / 7: 128 compute threads, half the signals per tile, 2 / 3
 // slots, 4 resident blocks per SM; 8: as 6 with registers capped for 5
-// resident blocks per SM)
-constexpr int kRaggedVariants = 9;
+// resident blocks per SM; 9: as 8, short lengths first in the work list)
+constexpr int kRaggedVariants = 10;
 constexpr int kRingVariant = 4;
 constexpr int kFirstProducerVariant = 5;
 constexpr int kDefaultRaggedVariant = 8;  // measured fastest on the mixed-length workload
+constexpr int kShortFirstVariant = 9;     // variant 8's kernel, short lengths first in the work list
+constexpr int kShortMaxLog2n = 6;
 // the variant ragged plans use when the caller names none (process-wide; the
 // autotuner's cached choice is applied through fft_set_default_ragged_variant)
 std::atomic<int> g_default_ragged_variant{kDefaultRaggedVariant};
@@ -124,12 +127,13 @@ constexpr int kRaggedThreads = 256;
 
 // the producer variants' per-length schedules for NTC compute threads: set 0
 // radices and elements per thread, NTC / 256 of its signals per tile, stage 0
-// read from the ring slot and every exchange inside it (XB = -1)
-template <int NTC, int L>
+// read from the ring slot and every exchange inside it (XB = -1); CH = 2
+// stores plainly (not evict-first), as the uniform defaults of N >= 128 do
+template <int NTC, int L, int CH = 0>
 struct SlotCfg {
     using B = typename RCfg<0, L>::type;
     using type = Cfg<L, B::E, B::S * NTC / kRaggedThreads, B::radix(0), B::radix(1), B::radix(2), B::radix(3), 2, 2,
-                     0, -1, 0>;
+                     0, -1, CH>;
     static_assert(type::NT == NTC, "one tile per compute group");
 };
 template <int NTC, int MINB>
@@ -513,7 +517,7 @@ __device__ __forceinline__ void slot_produce(const RaggedArgs& a, float2* ring, 
 
 // The body of the producer-warp kernels; the __global__ wrappers below differ
 // only in how they bound registers.
-template <int NTC, int SLOTS, int MINB, bool INV>
+template <int NTC, int SLOTS, int MINB, int CH, bool INV>
 __device__ __forceinline__ void ragged_slot_body(const RaggedArgs& a) {
     constexpr int kSlots = SLOTS;
     constexpr int kSlotTile = SlotShape<NTC, MINB>::kTile;
@@ -557,7 +561,7 @@ __device__ __forceinline__ void ragged_slot_body(const RaggedArgs& a) {
         switch (w.log2n) {
 #define GBFFT_SCASE(L)                                                                                       \
     case L:                                                                                                  \
-        slot_tile<typename SlotCfg<NTC, L>::type, INV>(a, w, ring + slot * kSlotTile, &empty[slot], off, dead); \
+        slot_tile<typename SlotCfg<NTC, L, CH>::type, INV>(a, w, ring + slot * kSlotTile, &empty[slot], off, dead); \
         break;
             GBFFT_SCASE(1) GBFFT_SCASE(2) GBFFT_SCASE(3) GBFFT_SCASE(4) GBFFT_SCASE(5) GBFFT_SCASE(6)
             GBFFT_SCASE(7) GBFFT_SCASE(8) GBFFT_SCASE(9) GBFFT_SCASE(10) GBFFT_SCASE(11)
@@ -576,15 +580,15 @@ __device__ __forceinline__ void ragged_slot_body(const RaggedArgs& a) {
 template <int NTC, int SLOTS, int MINB, bool INV>
 __global__ void __launch_bounds__(SlotShape<NTC, MINB>::kThreads, SlotShape<NTC, MINB>::kMinBlocks)
     fft_ragged_slot_kernel(RaggedArgs a) {
-    ragged_slot_body<NTC, SLOTS, MINB, INV>(a);
+    ragged_slot_body<NTC, SLOTS, MINB, 0, INV>(a);
 }
 
 // Registers capped at REGS per thread directly (80 leaves room for 5 blocks
 // of 160 threads per SM); the minimum-blocks form of the same budget left
 // the compiler at 72 registers with spills in the exchange loop.
-template <int NTC, int SLOTS, int REGS, bool INV>
+template <int NTC, int SLOTS, int REGS, int CH, bool INV>
 __global__ void __maxnreg__(REGS) fft_ragged_slot_kernel_capped(RaggedArgs a) {
-    ragged_slot_body<NTC, SLOTS, 5, INV>(a);
+    ragged_slot_body<NTC, SLOTS, 5, CH, INV>(a);
 }
 
 // ---------------------------------------------------------------------------
@@ -682,8 +686,11 @@ const void* ragged_kernel(int v, bool inv) {
             return inv ? reinterpret_cast<const void*>(&fft_ragged_slot_kernel<128, 3, 4, true>)
                        : reinterpret_cast<const void*>(&fft_ragged_slot_kernel<128, 3, 4, false>);
         case 8:
-            return inv ? reinterpret_cast<const void*>(&fft_ragged_slot_kernel_capped<128, 2, 80, true>)
-                       : reinterpret_cast<const void*>(&fft_ragged_slot_kernel_capped<128, 2, 80, false>);
+            return inv ? reinterpret_cast<const void*>(&fft_ragged_slot_kernel_capped<128, 2, 80, 0, true>)
+                       : reinterpret_cast<const void*>(&fft_ragged_slot_kernel_capped<128, 2, 80, 0, false>);
+        case 9:
+            return inv ? reinterpret_cast<const void*>(&fft_ragged_slot_kernel_capped<128, 2, 80, 0, true>)
+                       : reinterpret_cast<const void*>(&fft_ragged_slot_kernel_capped<128, 2, 80, 0, false>);
         default:
             return inv ? reinterpret_cast<const void*>(&fft_ragged_ring_kernel<true>)
                        : reinterpret_cast<const void*>(&fft_ragged_ring_kernel<false>);
@@ -750,14 +757,23 @@ fft_status_t ragged_create(const int64_t* offsets, int64_t count, int direction,
     st->begin = count > 0 ? offsets[0] : 0;
     st->end = count > 0 ? offsets[count] : 0;
 
-    // work list (longest length first: the producer variants' named barriers
-    // rely on that order, see slot_sync) and the bucketed offsets
+    // work list and the bucketed offsets.  Longest length first, so that the
+    // last items, which run while the machine drains, are short; variant 9
+    // takes the lengths up to 64 (tiles of many tiny signals, one bulk copy
+    // each) first instead, then the rest longest first, so the final items
+    // are tiles of 8-16 medium signals.  (The named barriers of the producer
+    // variants allow any order, see slot_sync.)
+    std::vector<int> order;
+    if (variant == kShortFirstVariant)
+        for (int L = GBFFT_MIN_LOG2N; L <= kShortMaxLog2n; ++L) order.push_back(L);
+    for (int L = GBFFT_MAX_LOG2N; L >= GBFFT_MIN_LOG2N; --L)
+        if (variant != kShortFirstVariant || L > kShortMaxLog2n) order.push_back(L);
     std::vector<RaggedItem> items;
     std::vector<int64_t> sig;
     sig.reserve((size_t)count);
     int tw_total = 0;
     int tw_off[GBFFT_MAX_LOG2N + 1] = {};
-    for (int L = GBFFT_MAX_LOG2N; L >= GBFFT_MIN_LOG2N; --L) {
+    for (const int L : order) {
         st->bucket_signals[L] = (int)buckets[L].size();
         if (buckets[L].empty()) continue;
         tw_off[L] = tw_total;
