@@ -4,20 +4,21 @@
 // Plan time (host): signals are bucketed by length; every bucket is cut into
 // tiles of S_N signals (the same per-length schedules as the uniform path,
 // re-shaped so that every length runs in a 256-thread block), and the tiles
-// become a device work list ordered from the longest length down.
+// become a device work list ordered from the longest length down (variant 9:
+// the lengths up to 64 first, then the rest longest first).
 //
-// Eight variants are compiled.  Bit 0 of variants 0..3 picks the schedule
+// Ten variants are compiled.  Bit 0 of variants 0..3 picks the schedule
 // set: set 0 keeps 16 complex elements per thread for N >= 32 (fewest
 // exchanges), set 1 keeps 8 (fewer registers, more resident blocks, finer
 // tiles).  Bit 1 picks how blocks get work: 0 = a shared counter (one
 // atomicAdd per item; fft_execute clears it with a memset node first), 1 =
 // static round robin with the next item's descriptor prefetched.  Variant 4
 // runs set 1 with a bulk-copy (TMA) ring that keeps the next item's signals in
-// flight.  Variants 5..8 run set 0 in ring slots that a producer warp fills
+// flight.  Variants 5..9 run set 0 in ring slots that a producer warp fills
 // (exchanges inside the slot): 5 with 256 compute threads and 2 slots, 6 with
-// 128 compute threads and 2 slots, 7 with 128 and 3 slots, 8 (the default) as
-// 6 with registers capped at 80 so that 5 blocks fit per SM, 9 the kernel of 8
-// with the lengths up to 64 first in the work list.
+// 128 compute threads and 2 slots, 7 with 128 and 3 slots, 8 as 6 with
+// registers capped at 80 so that 5 blocks fit per SM, 9 (the default) the
+// kernel of 8 with the lengths up to 64 first in the work list.
 // Variants 4..9 wait on mbarriers, with the same bounded waits, error word
 // and stall test mode as the uniform ring kernels.  Every step is
 // stream-ordered, so an execute can be captured in a CUDA graph.  The
@@ -108,7 +109,7 @@ GBFFT_RCFG(1, 11, 8, 1, 4, 8, 8, 8)
 constexpr int kRaggedVariants = 10;
 constexpr int kRingVariant = 4;
 constexpr int kFirstProducerVariant = 5;
-constexpr int kDefaultRaggedVariant = 8;  // measured fastest on the mixed-length workload
+constexpr int kDefaultRaggedVariant = 9;  // measured fastest on the mixed-length workload
 constexpr int kShortFirstVariant = 9;     // variant 8's kernel, short lengths first in the work list
 constexpr int kShortMaxLog2n = 6;
 // the variant ragged plans use when the caller names none (process-wide; the
