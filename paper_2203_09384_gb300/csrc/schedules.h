@@ -47,7 +47,7 @@
     GX(7, 2, 16, 16, 8, 16, 0, 0, 3, 2, 2, 0, 0) \
     GX(7, 3, 16, 32, 8, 16, 0, 0, 2, 0, 1, 0, 0) \
     GX(7, 4, 16, 32, 8, 16, 0, 0, 2, 0, 2, 0, 0) \
-    GX(8, 0, 16, 16, 16, 16, 0, 0, 1, 0, 0, 0, 2) \
+    GX(8, 17, 16, 16, 16, 16, 0, 0, 1, 0, 0, 0, 2) \
     GX(8, 7, 16, 8, 16, 16, 0, 0, 3, 2, 1, 0, 0) \
     GX(8, 8, 16, 8, 16, 16, 0, 0, 3, 2, 2, 0, 0) \
     GX(8, 3, 16, 16, 16, 16, 0, 0, 1, 0, 1, 0, 0) \
@@ -59,6 +59,10 @@
     GX(8, 1, 16, 8, 16, 16, 0, 0, 3, 2, 5, 0, 2) \
     GX(8, 12, 16, 8, 16, 16, 0, 0, 3, 2, 6, 0, 2) \
     GX(8, 13, 16, 16, 16, 16, 0, 0, 1, 0, 0, 3, 2) \
+    GX(8, 14, 16, 8, 16, 16, 0, 0, 3, 2, 0, 0, 2) \
+    GX(8, 15, 16, 8, 16, 16, 0, 0, 4, 2, 0, -1, 2) \
+    GX(8, 16, 16, 8, 16, 16, 0, 0, 5, 2, 0, -1, 2) \
+    GX(8, 0, 16, 16, 16, 16, 0, 0, 2, 2, 0, -1, 2) \
     GX(9, 0, 16, 8, 8, 8, 8, 0, 2, 0, 0, 0, 3) \
     GX(9, 1, 16, 8, 8, 8, 8, 0, 1, 0, 0, 0, 0) \
     GX(10, 0, 16, 2, 8, 16, 8, 0, 2, 2, 0, 0, 2) \
