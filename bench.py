@@ -248,7 +248,7 @@ def _time_ms(fn, stream, reps: int = 10, warmup: int = 3, inner: int = 1) -> flo
 EXTRAS = ("adjoint", "ragged", "precision")
 
 
-def run_extras(dev, stream, peak, which=EXTRAS):
+def run_extras(dev, stream, peak, which=EXTRAS, ragged_variant=None):
     """The other workloads of the hot path, each on its own synthetic data:
     the adjoint (autograd backward), ragged mixed lengths in one graph-captured
     launch, and FP16/BF16 tensor-core radix-16 stages against FP32."""
@@ -256,7 +256,7 @@ def run_extras(dev, stream, peak, which=EXTRAS):
     if "adjoint" in which:
         out["adjoint"] = extra_adjoint(dev, stream)
     if "ragged" in which:
-        out["ragged"] = extra_ragged(dev, stream)
+        out["ragged"] = extra_ragged(dev, stream, ragged_variant)
     if "precision" in which:
         out["precision"] = extra_precision(dev, stream, peak)
     return out
@@ -299,10 +299,11 @@ def extra_adjoint(dev, stream):
             "note": "step = forward FFT + torch loss ops + adjoint FFT kernel"}
 
 
-def extra_ragged(dev, stream):
+def extra_ragged(dev, stream, variant=None):
     """20000 signals, lengths 2^U{4..11}, seed 3: one ragged launch replayed
     from a CUDA graph, against one plain launch per length (also a graph) on
-    the same signals and a uniform N = 2048 call of the same element count."""
+    the same signals and a uniform N = 2048 call of the same element count.
+    The ragged variant is the tuner's pick unless `variant` names one."""
     import torch
 
     import paper_2203_09384_gb300 as gb
@@ -313,7 +314,10 @@ def extra_ragged(dev, stream):
     offs = synth.ragged_offsets(lengths)
     xr = synth.ragged_uniform(lengths, seed=3).to(dev)
     yr = torch.empty_like(xr)
-    tuned = autotune.tune_ragged(offs.numpy(), xr, yr, reps=10)
+    if variant is None:
+        tuned = autotune.tune_ragged(offs.numpy(), xr, yr, reps=10)
+    else:
+        tuned = {"best": int(variant), "ms": {}}
     rp = gb.RaggedPlan(offs.numpy(), variant=tuned["best"], device=dev)
     total = int(offs[-1])
     # the same signals grouped by length: one plain launch per length
@@ -657,7 +661,8 @@ def run_ours(args):
     }
     extras = [] if args.no_extras else [e for e in args.extras.split(",") if e]
     if extras:
-        line["extra"] = run_extras(dev, stream, peak, extras)
+        line["extra"] = run_extras(dev, stream, peak, extras,
+                                   None if args.ragged_variant < 0 else args.ragged_variant)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line))
@@ -730,6 +735,8 @@ def main(argv=None):
     ap.add_argument("--extras", default=",".join(EXTRAS),
                     help="comma list of the extra workloads to run (adjoint, ragged, precision)")
     ap.add_argument("--only-n", default="", help="comma list of lengths (profiling runs)")
+    ap.add_argument("--ragged-variant", type=int, default=-1,
+                    help="ragged variant of the ragged extra (profiling runs; default: the tuner's pick)")
     ap.add_argument("--elems", type=int, default=0, help="elements per length (profiling runs)")
     ap.add_argument("--variant", type=int, default=-1,
                     help="schedule variant of the length given by --only-n (profiling runs; default: the length's own)")
