@@ -17,8 +17,8 @@
 // flight.  Variants 5..9 run set 0 in ring slots that a producer warp fills
 // (exchanges inside the slot): 5 with 256 compute threads and 2 slots, 6 with
 // 128 compute threads and 2 slots, 7 with 128 and 3 slots, 8 as 6 with
-// registers capped at 80 so that 5 blocks fit per SM, 9 (the default) the
-// kernel of 8 with the lengths up to 64 first in the work list.
+// registers capped at 80, 9 (the default) the kernel of 8 with the lengths up
+// to 64 first in the work list.
 // Variants 4..9 wait on mbarriers, with the same bounded waits, error word
 // and stall test mode as the uniform ring kernels.  Every step is
 // stream-ordered, so an execute can be captured in a CUDA graph.  The
@@ -104,8 +104,8 @@ GBFFT_RCFG(1, 11, 8, 1, 4, 8, 8, 8)
 // schedule set 1 shapes fed by a bulk-copy (TMA) prefetch ring; variants 5..8:
 // set 0 shapes in ring slots filled by a producer warp (5: 256 compute threads
 // and 2 slots; 6 / 7: 128 compute threads, half the signals per tile, 2 / 3
-// slots, 4 resident blocks per SM; 8: as 6 with registers capped for 5
-// resident blocks per SM; 9: as 8, short lengths first in the work list)
+// slots, 4 resident blocks per SM; 8: as 6 with registers capped at 80;
+// 9: as 8, short lengths first in the work list)
 constexpr int kRaggedVariants = 10;
 constexpr int kRingVariant = 4;
 constexpr int kFirstProducerVariant = 5;
@@ -584,9 +584,11 @@ __global__ void __launch_bounds__(SlotShape<NTC, MINB>::kThreads, SlotShape<NTC,
     ragged_slot_body<NTC, SLOTS, MINB, 0, INV>(a);
 }
 
-// Registers capped at REGS per thread directly (80 leaves room for 5 blocks
-// of 160 threads per SM); the minimum-blocks form of the same budget left
-// the compiler at 72 registers with spills in the exchange loop.
+// Registers capped at REGS per thread directly.  (Registers are allocated per
+// SM sub-partition, 4 x 16K, a warp at a time: at 80 registers 4 blocks of 5
+// warps fit per SM, 5 would need 72 or fewer.  Measured: a 72-register form,
+// with the next item loaded late to avoid spills, ran 5 blocks per SM and was
+// no faster.)
 template <int NTC, int SLOTS, int REGS, int CH, bool INV>
 __global__ void __maxnreg__(REGS) fft_ragged_slot_kernel_capped(RaggedArgs a) {
     ragged_slot_body<NTC, SLOTS, 5, CH, INV>(a);
@@ -687,8 +689,6 @@ const void* ragged_kernel(int v, bool inv) {
             return inv ? reinterpret_cast<const void*>(&fft_ragged_slot_kernel<128, 3, 4, true>)
                        : reinterpret_cast<const void*>(&fft_ragged_slot_kernel<128, 3, 4, false>);
         case 8:
-            return inv ? reinterpret_cast<const void*>(&fft_ragged_slot_kernel_capped<128, 2, 80, 0, true>)
-                       : reinterpret_cast<const void*>(&fft_ragged_slot_kernel_capped<128, 2, 80, 0, false>);
         case 9:
             return inv ? reinterpret_cast<const void*>(&fft_ragged_slot_kernel_capped<128, 2, 80, 0, true>)
                        : reinterpret_cast<const void*>(&fft_ragged_slot_kernel_capped<128, 2, 80, 0, false>);
@@ -765,10 +765,11 @@ fft_status_t ragged_create(const int64_t* offsets, int64_t count, int direction,
     // are tiles of 8-16 medium signals.  (The named barriers of the producer
     // variants allow any order, see slot_sync.)
     std::vector<int> order;
-    if (variant == kShortFirstVariant)
+    const bool short_first = variant >= kShortFirstVariant;
+    if (short_first)
         for (int L = GBFFT_MIN_LOG2N; L <= kShortMaxLog2n; ++L) order.push_back(L);
     for (int L = GBFFT_MAX_LOG2N; L >= GBFFT_MIN_LOG2N; --L)
-        if (variant != kShortFirstVariant || L > kShortMaxLog2n) order.push_back(L);
+        if (!short_first || L > kShortMaxLog2n) order.push_back(L);
     std::vector<RaggedItem> items;
     std::vector<int64_t> sig;
     sig.reserve((size_t)count);
