@@ -21,6 +21,10 @@
  *
  * Every call returns an fft_status_t.  Out-parameters are written only on
  * FFT_OK.  No call here aborts, prints, or throws.
+ *
+ * Test hook: with GBFFT_TEST_FAIL_ALLOC=k in the environment, the k-th device
+ * allocation of each plan-creation call reports failure (FFT_ERR_ALLOC)
+ * without allocating, so tests can take every allocation-failure path.
  */
 #ifndef GBFFT_H
 #define GBFFT_H

@@ -805,7 +805,7 @@ fft_status_t ragged_create(const int64_t* offsets, int64_t count, int direction,
     const size_t off_sig = off_items + ((items.size() * sizeof(RaggedItem) + 255) / 256) * 256;
     const size_t off_tw = off_sig + ((sig.size() * sizeof(int64_t) + 255) / 256) * 256;
     const size_t bytes = off_tw + (size_t)tw_total * sizeof(float2) + 16;
-    if (cudaMalloc(&st->dmem, bytes) != cudaSuccess) {
+    if (plan_malloc(&st->dmem, bytes) != cudaSuccess) {
         cudaGetLastError();
         delete st;
         return FFT_ERR_ALLOC;

@@ -98,6 +98,20 @@ constexpr uint64_t kDefaultWaitNs = 4000000000ull;  // bounded device waits: 4 s
 }  // namespace
 
 namespace gbfft {
+namespace {
+thread_local int t_plan_allocs = 0;
+}
+void begin_plan_allocs() { t_plan_allocs = 0; }
+cudaError_t plan_malloc(void** ptr, size_t bytes) {
+    ++t_plan_allocs;
+    const char* fail = getenv("GBFFT_TEST_FAIL_ALLOC");
+    if (fail && atoi(fail) == t_plan_allocs) {
+        *ptr = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(ptr, bytes);
+}
+
 // Registry lookup for other host translation units: the kernel entry of
 // `variant` (or of the length's current default when variant < 0), or NULL.
 const KernelEntry* lookup_entry(int log2n, int variant) {
@@ -190,7 +204,7 @@ fft_status_t create_staging(gbfft_plan* p) {
     if (chunk < 1) chunk = 1;
     p->chunk_signals = chunk;
     p->stages = 3;
-    if (cudaMalloc(&p->d_stage, (size_t)(3 * chunk * sig_bytes)) != cudaSuccess) {
+    if (gbfft::plan_malloc(reinterpret_cast<void**>(&p->d_stage), (size_t)(3 * chunk * sig_bytes)) != cudaSuccess) {
         cudaGetLastError();
         p->d_stage = nullptr;
         p->stages = 0;
@@ -288,6 +302,7 @@ fft_status_t fft_validate(int64_t n, int64_t batch, int direction, int dtype, ui
 fft_status_t fft_plan_create_ex(int64_t n, int64_t batch, int direction, int dtype, uint32_t flags,
                                 fft_plan_t* plan) {
     if (!plan) return FFT_ERR_INVALID_VALUE;
+    gbfft::begin_plan_allocs();
     fft_status_t st = fft_validate(n, batch, direction, dtype, flags);
     if (st != FFT_OK) return st;
 
@@ -347,7 +362,7 @@ fft_status_t fft_plan_create_ex(int64_t n, int64_t batch, int direction, int dty
     const size_t tw_bytes = (size_t)e->twiddles * 2 * sizeof(float);
     const size_t alloc = tw_bytes + 256;
     void* dmem = nullptr;
-    if (cudaMalloc(&dmem, alloc) != cudaSuccess) {
+    if (gbfft::plan_malloc(&dmem, alloc) != cudaSuccess) {
         cudaGetLastError();
         delete p;
         return FFT_ERR_ALLOC;
@@ -426,6 +441,7 @@ int fft_ragged_variant_count(void) { return gbfft::ragged_variant_count(); }
 fft_status_t fft_plan_create_ragged(const int64_t* offsets_host, int64_t count, int direction, int dtype,
                                     uint32_t flags, fft_plan_t* plan) {
     if (!plan) return FFT_ERR_INVALID_VALUE;
+    gbfft::begin_plan_allocs();
     if (direction != FFT_FORWARD && direction != FFT_INVERSE) return FFT_ERR_INVALID_VALUE;
     if (dtype != FFT_C64 && dtype != FFT_C64_TC_F16 && dtype != FFT_C64_TC_BF16 && dtype != FFT_C32)
         return FFT_ERR_INVALID_VALUE;

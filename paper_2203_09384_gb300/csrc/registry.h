@@ -35,6 +35,14 @@ struct KernelEntry {
     void (*fill_twiddles)(float* host);
 };
 
+// Device allocation of plan creation (host).  Every plan-creation call starts
+// its count with begin_plan_allocs(); with GBFFT_TEST_FAIL_ALLOC=k in the
+// environment (a test hook for failure detection) the k-th allocation of the
+// call reports failure without allocating, so the tests can take every
+// allocation-failure path of plan creation.
+void begin_plan_allocs();
+cudaError_t plan_malloc(void** ptr, size_t bytes);
+
 // Registry lookup (host): the entry of `variant`, or of the length's current
 // default when variant < 0; NULL when there is none.
 const KernelEntry* lookup_entry(int log2n, int variant);

@@ -6,6 +6,7 @@ completion) issue nothing, so each wait runs out after the plan's wait limit (1 
 kernel records FFT_ERR_TIMEOUT in the plan's error word and finishes.  The
 context must stay usable afterwards.
 """
+import numpy as np
 import pytest
 import torch
 
@@ -130,4 +131,45 @@ def test_wait_limit_validation():
     plan = gb.Plan(2048, 8)
     with pytest.raises(gb.FFTError):
         plan.set_wait_limit(0)
+    plan.close()
+
+
+@pytest.mark.parametrize("kind,k", [("plain", 1), ("staging", 1), ("staging", 2), ("ragged", 1)])
+def test_every_allocation_failure_of_plan_creation(kind, k, monkeypatch):
+    """GBFFT_TEST_FAIL_ALLOC=k (a host-side test hook) makes the k-th device
+    allocation of a plan-creation call fail without allocating.  Each failure
+    path returns FFT_ERR_ALLOC, frees what the call had already allocated (200
+    failing calls leave the device's free memory where it was), and the next
+    plan, made without the hook, is correct."""
+    n, batch = 256, 4096
+    offsets = np.concatenate([[0], np.cumsum([256, 2048, 16] * 10)])
+
+    def create():
+        if kind == "ragged":
+            return gb.RaggedPlan(offsets)
+        return gb.Plan(n, batch, host_staging=kind == "staging")
+
+    torch.cuda.synchronize()
+    free_before = torch.cuda.mem_get_info()[0]
+    monkeypatch.setenv("GBFFT_TEST_FAIL_ALLOC", str(k))
+    for _ in range(200):
+        with pytest.raises(gb.FFTError) as e:
+            create()
+        assert e.value.status == _abi.STATUS_CODE["FFT_ERR_ALLOC"]
+    monkeypatch.setenv("GBFFT_TEST_FAIL_ALLOC", str(k + 2))  # past the call's last allocation: no failure
+    create().close()
+    monkeypatch.delenv("GBFFT_TEST_FAIL_ALLOC")
+    torch.cuda.synchronize()
+    assert free_before - torch.cuda.mem_get_info()[0] < (4 << 20)
+    plan = create()
+    if kind == "ragged":
+        x = synth.uniform(1, int(offsets[-1]), seed=9).reshape(-1).cuda()
+        y = plan.execute(x)
+        first = slice(0, 256)
+        assert max_rel_l2(to_np(y[first])[None], oracle.reference(x[first].cpu().numpy()[None])) <= FP32_TOL
+    else:
+        x = synth.uniform(batch, n, seed=9).cuda()
+        y = plan.execute(x)
+        assert max_rel_l2(to_np(y[:32]), oracle.reference(x[:32].cpu().numpy())) <= FP32_TOL
+    assert plan.error() == 0
     plan.close()
