@@ -476,6 +476,14 @@ def run_reference(args):
     return 0
 
 
+def rank_input(rank: int, elems: int, device="cpu"):
+    """The batch one rank transforms: its own seeded U[-1, 1] draw (seed
+    1 + rank), so ranks work on different data and exchange none of it (the
+    sweep is weak scaling: every rank moves the same bytes)."""
+    import synth
+    return synth.uniform(1, elems, seed=1 + rank, device=device).reshape(-1)
+
+
 def reduce_max_over_ranks(ms: float, device=None) -> float:
     """The slowest rank's time (the job is done when every rank is done)."""
     import torch
@@ -514,7 +522,7 @@ def run_ours(args):
         ELEMS = int(args.elems)
     if args.only_n:
         LOG2NS = [int(math.log2(int(v))) for v in args.only_n.split(",")]
-    x = synth.uniform(1, ELEMS, seed=1 + rank, device=dev).reshape(-1)
+    x = rank_input(rank, ELEMS, dev)
     variant = None if args.variant < 0 else args.variant
     plans = {k: gb.Plan(2 ** k, ELEMS // 2 ** k, device=dev, dtype=args.dtype, variant=variant) for k in LOG2NS}
     c32 = args.dtype == "c32"
