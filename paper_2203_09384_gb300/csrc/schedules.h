@@ -125,13 +125,14 @@
     CX(5, 4, 16, 128, 8, 4, 0, 0, 1, 0, 0)       \
     CX(6, 1, 16, 64, 8, 8, 0, 0, 1, 0, 0)        \
     CX(7, 5, 16, 32, 8, 16, 0, 0, 1, 0, 0)       \
-    CX(8, 5, 16, 16, 16, 16, 0, 0, 3, 2, 1)      \
+    CX(8, 18, 16, 16, 16, 16, 0, 0, 3, 2, 1)      \
     CX(8, 6, 16, 16, 16, 16, 0, 0, 1, 0, 0)      \
     CX(9, 2, 16, 8, 8, 8, 8, 0, 2, 0, 0)         \
     CX(10, 8, 16, 2, 8, 16, 8, 0, 2, 3, 0)       \
     CX(10, 9, 16, 2, 8, 16, 8, 0, 2, 0, 0)       \
     CX(11, 8, 16, 1, 8, 16, 16, 0, 3, 3, 0)      \
-    CX(11, 9, 16, 1, 8, 16, 16, 0, 3, 0, 0)
+    CX(11, 9, 16, 1, 8, 16, 16, 0, 3, 0, 0)      \
+    CX(8, 5, 16, 8, 16, 16, 0, 0, 5, 2, 1)
 
 // complex32 one-thread-per-signal rows (N <= 32): SCX(log2N, variant, warps
 // per block, 32-signal groups per warp tile, cache hints)

@@ -65,7 +65,7 @@ def test_complex32_registry():
     for k in range(1, 12):
         n = 2 ** k
         kinds = [_abi.lib().fft_variant_dtype(n, v) for v in range(_abi.fft_variant_count(n))]
-        assert 1 <= kinds.count(_abi.FFT_C32) <= 2
+        assert kinds.count(_abi.FFT_C32) >= 1
         assert kinds[_abi.fft_get_default_variant(n)] == _abi.FFT_C64
     assert _abi.fft_validate(64, 1, 0, _abi.FFT_C32, _abi.FFT_FLAG_HOST_STAGING) == \
         _abi.STATUS_CODE["FFT_ERR_UNSUPPORTED"]
@@ -151,3 +151,4 @@ def test_schedule_variant_numbers_are_unique():
     for k in range(1, 12):
         used = {v for (L, v) in seen if L == k}
         assert _abi.fft_variant_count(2 ** k) == max(used) + 1
+        assert used == set(range(max(used) + 1)), f"N=2^{k}: variant numbers with no row"
