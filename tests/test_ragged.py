@@ -144,6 +144,35 @@ def test_every_length_mixed_inverse_inplace():
             plan.close()
 
 
+def test_runs_of_equal_lengths():
+    """Runs of equal lengths, so that some tiles are one back-to-back span
+    (fetched by a single bulk copy, offsets computed) and others are not:
+    runs longer and shorter than a tile, broken by other lengths, every
+    variant, forward and inverse, against the oracle."""
+    rng = np.random.default_rng(41)
+    runs = []
+    for _ in range(60):
+        n = int(2 ** rng.integers(1, 12))
+        runs.append(np.full(int(rng.integers(1, 300 if n <= 64 else 12)), n))
+    runs.append(np.full(700, 16))  # several whole 16-point tiles
+    lengths = np.concatenate(runs)
+    offsets = np.concatenate([[2], 2 + np.cumsum(lengths)])
+    x = synth.uniform(1, int(offsets[-1]), seed=42).reshape(-1)
+    x[:2] = 0
+    for inverse in (False, True):
+        want = oracle_ragged(x.numpy(), offsets, inverse)
+        for variant in range(gb.fft_ragged_variant_count()):
+            plan = gb.RaggedPlan(offsets, inverse=inverse, variant=variant)
+            y = torch.zeros_like(x).cuda()
+            plan.execute(x.cuda(), y)
+            torch.cuda.synchronize()
+            assert _abi.lib().fft_plan_get_error(plan.handle) == 0
+            plan.close()
+            got = y.cpu().numpy().astype(np.complex128)
+            assert per_signal_max_err(got, want, offsets) <= FP32_TOL, (inverse, variant)
+            assert np.all(got[:2] == 0)
+
+
 def test_ragged_edge_cases():
     # one signal; empty list
     x = synth.uniform(1, 64, seed=1).reshape(-1).cuda()
