@@ -78,7 +78,7 @@
     GX(10, 12, 16, 2, 8, 16, 8, 0, 5, 2, 2, -2, 0) \
     GX(10, 13, 16, 2, 8, 16, 8, 0, 4, 2, 1, 1, 0) \
     GX(10, 14, 16, 2, 8, 16, 8, 0, 4, 2, 2, 1, 0) \
-    GX(11, 0, 16, 1, 8, 16, 16, 0, 5, 2, 0, -1, 2) \
+    GX(11, 0, 16, 1, 8, 16, 16, 0, 4, 2, 0, -1, 2) \
     GX(11, 1, 16, 1, 8, 16, 16, 0, 1, 0, 0, 0, 0) \
     GX(11, 2, 16, 1, 8, 16, 16, 0, 2, 3, 0, 0, 0) \
     GX(11, 3, 16, 2, 8, 16, 16, 0, 1, 2, 0, 0, 0) \
@@ -94,7 +94,8 @@
     GX(11, 4, 16, 1, 8, 16, 16, 0, 5, 2, 1, -3, 2) \
     GX(11, 5, 16, 1, 8, 16, 16, 0, 5, 2, 2, -3, 2) \
     GX(11, 17, 16, 1, 8, 16, 16, 0, 5, 2, 5, -3, 2) \
-    GX(11, 18, 16, 1, 8, 16, 16, 0, 5, 2, 6, -3, 2)
+    GX(11, 18, 16, 1, 8, 16, 16, 0, 5, 2, 6, -3, 2) \
+    GX(11, 19, 16, 1, 8, 16, 16, 0, 5, 2, 0, -1, 2)
 
 #define GBFFT_SMALL_SCHEDULES(SX) \
     SX(1, 0, 8, 1, 3)                \
