@@ -239,13 +239,38 @@ __device__ __forceinline__ void st_stream4v(float4* p, float4 a) {
     }
 }
 
-// Shared-memory swizzle at 8-byte granularity: rows of 16 elements (128 B)
-// are XOR-permuted by their row index.  tests/test_bank_model.py replays every
-// schedule's exchanges under it and counts the wavefronts (64-bit accesses
-// resolve per half-warp), in agreement with ncu.
-__device__ __forceinline__ int swz8(int a) { return a ^ ((a >> 4) & 15); }
-// Same idea at 16-byte granularity (rows of 8 float4 slots).
-__device__ __forceinline__ int swz16(int a) { return a ^ ((a >> 3) & 7); }
+// Shared-memory swizzle at 8-byte granularity: the 16 elements (128 B) of row
+// `row = a >> 4` are XOR-permuted by the row index, for transforms of length
+// N = 32 and 64 by row ^ (row >> 2).  By the row alone their exchanges
+// (signals starting every 2 or 4 rows) take 1.5x the conflict-free
+// wavefronts; with row >> 2 folded in none conflicts.  Every other length is
+// conflict free (or at its bound) either way and keeps the cheaper form:
+// measured, the folded form cost the N = 2048 ring kernel 1.4 points.
+// tests/test_bank_model.py replays every schedule's exchanges under it and
+// counts the wavefronts (64-bit accesses resolve per half-warp), in agreement
+// with ncu.
+template <int N>
+__device__ __forceinline__ int swz8(int a) {
+    const int row = a >> 4;
+    if constexpr (N == 32 || N == 64) {
+        return a ^ ((row ^ (row >> 2)) & 15);
+    } else {
+        return a ^ (row & 15);
+    }
+}
+// Same idea at 16-byte granularity: the 8 float4 slots of row `row = a >> 3`
+// XOR-permuted by the row index, for N = 32 by row ^ (row >> 3) (by the row
+// alone, the one-thread-per-signal reads of 32-point signals, 16 slots apart,
+// meet 1.5x conflicts; the shorter lengths are conflict free either way).
+template <int N>
+__device__ __forceinline__ int swz16(int a) {
+    const int row = a >> 3;
+    if constexpr (N == 32) {
+        return a ^ ((row ^ (row >> 3)) & 7);
+    } else {
+        return a ^ (row & 7);
+    }
+}
 
 // ---------------------------------------------------------------------------
 // Bulk copy (TMA, non-tensor form) and mbarrier primitives, inline PTX
@@ -872,7 +897,7 @@ __device__ __forceinline__ void scatter(const float2 (&v)[C::E], float2* buf, in
 #pragma unroll
         for (int q = 0; q < R; ++q) {
             if (!dbg_ok(base + q * Ns >= 0 && base + q * Ns < C::S * C::N)) continue;
-            buf[swz8(base + q * Ns)] = v[c * R + q];
+            buf[swz8<C::N>(base + q * Ns)] = v[c * R + q];
         }
     }
 }
@@ -890,8 +915,8 @@ __device__ __forceinline__ void gather(float2 (&v)[C::E], float2* buf, int sb, i
         for (int r = 0; r < R; ++r) {
             const int a = sb + j + r * stride;
             if (!dbg_ok(a >= 0 && a < C::S * C::N)) continue;
-            v[c * R + r] = buf[swz8(a)];
-            GBFFT_DBG_ONLY(buf[swz8(a)] = make_float2(__int_as_float(0x7fc00000), __int_as_float(0x7fc00000));)
+            v[c * R + r] = buf[swz8<C::N>(a)];
+            GBFFT_DBG_ONLY(buf[swz8<C::N>(a)] = make_float2(__int_as_float(0x7fc00000), __int_as_float(0x7fc00000));)
         }
     }
 }
@@ -1325,7 +1350,7 @@ __global__ void __launch_bounds__(SC::NT) fft_small_kernel(const float2* in, flo
 #pragma unroll
         for (int i = 0; i < U * H; ++i) {
             const int p = lane + 32 * i;
-            if (p < valid4) sm[swz16(p)] = ld_stream4v<SC::CH>(src + p);
+            if (p < valid4) sm[swz16<SC::N>(p)] = ld_stream4v<SC::CH>(src + p);
         }
         __syncwarp();
 #pragma unroll
@@ -1334,7 +1359,7 @@ __global__ void __launch_bounds__(SC::NT) fft_small_kernel(const float2* in, flo
             float2 v[N];
 #pragma unroll
             for (int i = 0; i < H; ++i) {
-                float4 f = sm[swz16(sig * H + i)];
+                float4 f = sm[swz16<SC::N>(sig * H + i)];
                 v[2 * i] = make_float2(f.x, INV ? -f.y : f.y);
                 v[2 * i + 1] = make_float2(f.z, INV ? -f.w : f.w);
             }
@@ -1343,13 +1368,13 @@ __global__ void __launch_bounds__(SC::NT) fft_small_kernel(const float2* in, flo
             for (int i = 0; i < N; ++i) v[i] = make_float2(v[i].x * scale, (INV ? -v[i].y : v[i].y) * scale);
 #pragma unroll
             for (int i = 0; i < H; ++i)
-                sm[swz16(sig * H + i)] = make_float4(v[2 * i].x, v[2 * i].y, v[2 * i + 1].x, v[2 * i + 1].y);
+                sm[swz16<SC::N>(sig * H + i)] = make_float4(v[2 * i].x, v[2 * i].y, v[2 * i + 1].x, v[2 * i + 1].y);
         }
         __syncwarp();
 #pragma unroll
         for (int i = 0; i < U * H; ++i) {
             const int p = lane + 32 * i;
-            if (p < valid4) st_stream4v<SC::CH>(dst + p, sm[swz16(p)]);
+            if (p < valid4) st_stream4v<SC::CH>(dst + p, sm[swz16<SC::N>(p)]);
         }
         __syncwarp();
     }
@@ -1656,10 +1681,10 @@ __global__ void __launch_bounds__(SC::NT)
 #pragma unroll
         for (int i = 0; i < (P + 31) / 32; ++i) {
             const int p = lane + 32 * i;
-            if (p < full) sm[swz16(p)] = ld_stream4v<SC::CH>(src + p);
+            if (p < full) sm[swz16<N>(p)] = ld_stream4v<SC::CH>(src + p);
         }
         if (N == 2 && lane == 0 && (valid_e & 3))  // odd signal count: the last signal is half a piece
-            reinterpret_cast<float2*>(sm + swz16(full))[0] =
+            reinterpret_cast<float2*>(sm + swz16<N>(full))[0] =
                 *reinterpret_cast<const float2*>(in + first * N + 4 * full);
         __syncwarp();
 #pragma unroll
@@ -1671,14 +1696,14 @@ __global__ void __launch_bounds__(SC::NT)
             if constexpr (N >= 4) {
 #pragma unroll
                 for (int i = 0; i < N / 4; ++i) {
-                    const float4 f = sm[swz16(sg * (N / 4) + i)];
+                    const float4 f = sm[swz16<N>(sg * (N / 4) + i)];
                     v[4 * i + 0] = __half22float2(bits_h2(f.x));
                     v[4 * i + 1] = __half22float2(bits_h2(f.y));
                     v[4 * i + 2] = __half22float2(bits_h2(f.z));
                     v[4 * i + 3] = __half22float2(bits_h2(f.w));
                 }
             } else {
-                const float2 f = reinterpret_cast<const float2*>(sm + swz16(sg >> 1))[sg & 1];
+                const float2 f = reinterpret_cast<const float2*>(sm + swz16<N>(sg >> 1))[sg & 1];
                 v[0] = __half22float2(bits_h2(f.x));
                 v[1] = __half22float2(bits_h2(f.y));
             }
@@ -1698,9 +1723,9 @@ __global__ void __launch_bounds__(SC::NT)
             if constexpr (N >= 4) {
 #pragma unroll
                 for (int i = 0; i < N / 4; ++i)
-                    sm[swz16(sg * (N / 4) + i)] = make_float4(hw[4 * i], hw[4 * i + 1], hw[4 * i + 2], hw[4 * i + 3]);
+                    sm[swz16<N>(sg * (N / 4) + i)] = make_float4(hw[4 * i], hw[4 * i + 1], hw[4 * i + 2], hw[4 * i + 3]);
             } else {
-                reinterpret_cast<float2*>(sm + swz16(sg >> 1))[sg & 1] = make_float2(hw[0], hw[1]);
+                reinterpret_cast<float2*>(sm + swz16<N>(sg >> 1))[sg & 1] = make_float2(hw[0], hw[1]);
             }
             if (act) out_exp[first + sg] = (int8_t)o.e;
         }
@@ -1708,10 +1733,10 @@ __global__ void __launch_bounds__(SC::NT)
 #pragma unroll
         for (int i = 0; i < (P + 31) / 32; ++i) {
             const int p = lane + 32 * i;
-            if (p < full) st_stream4v<SC::CH>(dst + p, sm[swz16(p)]);
+            if (p < full) st_stream4v<SC::CH>(dst + p, sm[swz16<N>(p)]);
         }
         if (N == 2 && lane == 0 && (valid_e & 3))
-            *reinterpret_cast<float2*>(out + first * N + 4 * full) = reinterpret_cast<const float2*>(sm + swz16(full))[0];
+            *reinterpret_cast<float2*>(out + first * N + 4 * full) = reinterpret_cast<const float2*>(sm + swz16<N>(full))[0];
         __syncwarp();
     }
 }

@@ -101,9 +101,9 @@ def replay(N, E, S, radix, pipe, x, plant=None, shuffle=False):
                     j = bfly(s - 1, t, c)
                     base = sb + (j // Nsp) * (Nsp * Rp) + (j % Nsp)
                     for q in range(Rp):
-                        a = swz8(base + q * Nsp)
+                        a = swz8(base + q * Nsp, N)
                         if plant == "scatter":  # written with the read pattern
-                            a = swz8(sb + j + q * (N // Rp))
+                            a = swz8(sb + j + q * (N // Rp), N)
                         assert a not in buf, f"stage {s}: slot {a} written twice"
                         assert 0 <= a < S * N, f"stage {s}: slot {a} outside the tile"
                         buf[a] = v[tid, c * Rp + q]
@@ -113,7 +113,7 @@ def replay(N, E, S, radix, pipe, x, plant=None, shuffle=False):
                 for c in range(K):
                     j = bfly(s, t, c)
                     for r in range(R):
-                        a = swz8(sb + j + r * stride)
+                        a = swz8(sb + j + r * stride, N)
                         assert a in buf, f"stage {s}: slot {a} read before it is written"
                         v[tid, c * R + r] = buf[a]
         w = np.exp(-2j * np.pi * np.outer(np.arange(R), np.arange(R)) / R)
