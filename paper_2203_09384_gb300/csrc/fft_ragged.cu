@@ -22,7 +22,9 @@
 // A tile whose signals lie back to back (runs of one length in the input)
 // is marked at plan time: its threads compute their offsets instead of
 // loading them, and the bulk-copy variants fetch a tile of short signals in
-// 2 KB copies rather than one copy per signal.
+// 2 KB copies rather than one copy per signal.  The producer variants place
+// the signals of any other tile of N = 4..128 with a gap in the ring slot, so
+// that stage 0 reads them without shared-memory bank conflicts (slot_pad).
 // Variants 4..9 wait on mbarriers, with the same bounded waits, error word
 // and stall test mode as the uniform ring kernels.  Every step is
 // stream-ordered, so an execute can be captured in a CUDA graph.  The
@@ -149,7 +151,9 @@ struct SlotCfg {
 };
 template <int NTC, int MINB>
 struct SlotShape {
-    static constexpr int kTile = NTC * 16;        // complex elements per tile (S * N) at most
+    // complex elements of a ring slot: a tile (S * N <= NTC * 16) plus the
+    // stage-0 padding of scattered short signals (S * T = NTC, see slot_pad)
+    static constexpr int kTile = NTC * 17;
     static constexpr int kThreads = NTC + 32;     // compute threads + the producer warp
     static constexpr int kMinBlocks = MINB;       // resident blocks per SM asked of the compiler
 };
@@ -447,10 +451,53 @@ __device__ __forceinline__ void slot_stages(float2 (&v)[C::E], float2* b, int sb
     }
 }
 
+// Stage-0 padding in the ring slot.  Stage 0 reads a tile as the bulk copies
+// wrote it, without a swizzle: with signals of N = 4..128 packed every N
+// elements, the threads of a half-warp (several signals, T threads each) hit
+// the same few banks (2-8 way, CPU bank model).  So the producer places the
+// signals of a tile of scattered signals (one copy per signal anyway) every
+// N + T elements: consecutive signals then start T bank slots apart and
+// stage 0 reads without conflicts.  The exchanges after it use the dense
+// layout again, behind a barrier of all compute threads.  Back-to-back tiles
+// keep the dense layout and their 2 KB copies; N = 2 has one stage.
+template <class C>
+constexpr int slot_pad_of() {
+    return C::LOG2N >= 2 && C::LOG2N <= 7 ? C::T : 0;
+}
+template <int NTC>
+__device__ __forceinline__ int slot_pad(int log2n) {
+    switch (log2n) {
+#define GBFFT_SPAD(L) \
+    case L: return slot_pad_of<typename SlotCfg<NTC, L>::type>();
+        GBFFT_SPAD(2) GBFFT_SPAD(3) GBFFT_SPAD(4) GBFFT_SPAD(5) GBFFT_SPAD(6) GBFFT_SPAD(7)
+#undef GBFFT_SPAD
+        default: return 0;
+    }
+}
+
+// stage-0 inputs from signal `sl` of a tile laid out every `pitch` elements
+template <class C, bool INV>
+__device__ __forceinline__ void slot_gather0(float2 (&v)[C::E], const float2* tile, int sb, int t) {
+    constexpr int R = C::radix(0);
+    constexpr int K = C::E / R;
+    constexpr int stride = C::N / R;
+#pragma unroll
+    for (int c = 0; c < K; ++c) {
+        const int j = bfly<C, 0>(t, c);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            if (!dbg_ok(sb + j + r * stride < C::NT * 17)) continue;
+            const float2 x = tile[sb + j + r * stride];
+            v[c * R + r] = INV ? conj2(x) : x;
+        }
+    }
+}
+
 template <class C, bool INV>
 __device__ __forceinline__ void slot_tile(const RaggedArgs& a, const RaggedItem& w, float2* slot, uint64_t* empty,
                                           int64_t off, bool dead) {
     static_assert(C::S * C::N <= C::NT * 16, "a tile must fit a ring slot");
+    static_assert(C::S * (C::N + slot_pad_of<C>()) <= C::NT * 17, "a padded tile must fit a ring slot");
     const int tid = threadIdx.x;
     const int sl = tid / C::T;
     const int t = tid % C::T;
@@ -459,8 +506,15 @@ __device__ __forceinline__ void slot_tile(const RaggedArgs& a, const RaggedItem&
     const float scale = a.scale_mode ? 1.0f / (float)C::N : 1.0f;
     TcCtx tc;  // FP32 butterflies only
     float2 v[C::E];
-    gather_tile<C, INV>(v, slot, sl * C::N, t);
+    constexpr int kPad = slot_pad_of<C>();
+    const bool padded = kPad != 0 && !w.contig && w.count > 1;  // the same for every compute thread
+    slot_gather0<C, INV>(v, slot, sl * (C::N + (padded ? kPad : 0)), t);
     twist_and_dft<C, 0>(v, t, tw, tc);
+    if constexpr (kPad != 0) {
+        // the dense exchanges below overwrite other signals' padded inputs:
+        // every compute thread must have read its own first
+        if (padded) asm volatile("bar.sync %0, %1;" ::"n"(bar_base<C::NT, 2 * C::NT>()), "n"(C::NT) : "memory");
+    }
     slot_stages<C, 1>(v, slot, sl * C::N, t, tw, tc);
     // this thread is done with the slot: order its shared-memory accesses
     // before the producer's next copy into it; once the whole warp is, one
@@ -528,8 +582,10 @@ __device__ __forceinline__ void slot_produce(const RaggedArgs& a, float2* ring, 
             for (int j = lane * kSpanChunk; j < total; j += 32 * kSpanChunk)
                 bulk_copy_g2s(dst + j, a.in + w.off0 + j, (uint32_t)(min(kSpanChunk, total - j) * 8), &full[slot]);
         } else {
+            // scattered signals, one copy each, every n + pad elements (slot_pad)
+            const int pitch = n + (w.count > 1 ? slot_pad<NTC>(w.log2n) : 0);
             for (int j = lane; j < w.count; j += 32)
-                bulk_copy_g2s(dst + j * n, a.in + (j == 0 ? w.off0 : a.sig_off[w.first + j]), (uint32_t)(n * 8),
+                bulk_copy_g2s(dst + j * pitch, a.in + (j == 0 ? w.off0 : a.sig_off[w.first + j]), (uint32_t)(n * 8),
                               &full[slot]);
         }
         if (nx >= a.n_items) break;
@@ -722,7 +778,7 @@ const void* ragged_kernel(int v, bool inv) {
 }
 int ragged_smem(int v) {
     if (v == kRingVariant) return 4 * kRingTile * (int)sizeof(float2) + 16;
-    if (is_producer_variant(v)) return producer_slots(v) * producer_group(v) * 16 * (int)sizeof(float2) + 2 * producer_slots(v) * 8;
+    if (is_producer_variant(v)) return producer_slots(v) * producer_group(v) * 17 * (int)sizeof(float2) + 2 * producer_slots(v) * 8;
     return schedule_set(v) == 0 ? ragged_smem_bytes<0>() : ragged_smem_bytes<1>();
 }
 

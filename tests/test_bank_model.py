@@ -196,3 +196,46 @@ def test_fp32_exchange_factors_stay_bounded():
         assert f <= 1.5 + 1e-9, (row, f)
     for row in small_rows():
         assert small_factor(row) <= 1.5 + 1e-9, row
+
+# ---------------------------------------------------------------------------
+# Ragged producer-warp kernel (csrc/fft_ragged.cu): stage 0 reads a tile as the
+# bulk copies wrote it.  Set 0 of its per-length table, on 128 compute
+# threads (half the signals of each 256-thread row); a tile of scattered
+# signals of N = 4..128 is placed every N + T elements (slot_pad), T = the
+# signal's threads.
+# ---------------------------------------------------------------------------
+RAGGED = os.path.join(os.path.dirname(SCHEDULES), "fft_ragged.cu")
+
+
+def ragged_set0_rows():
+    text = open(RAGGED).read()
+    rows = {}
+    for m in re.finditer(r"^GBFFT_RCFG\(0, ([-\d,\s]+)\)", text, re.M):
+        L, E, S, r0, r1, r2, r3 = (int(v) for v in m.group(1).split(","))
+        rows[L] = {"N": 1 << L, "E": E, "S": S // 2, "radix": [r for r in (r0, r1, r2, r3) if r]}
+    return rows
+
+
+def ragged_stage0_factor(row, pad: int) -> float:
+    N, E, S, R = row["N"], row["E"], row["S"], row["radix"][0]
+    T, K = N // E, E // R
+    accesses = []
+    for w in range(0, T * S, 32):
+        for c in range(K):
+            for r in range(R):  # butterfly t + T c of the in-slot stage-0 mapping
+                accesses.append([(tid // T) * (N + pad) + (tid % T) + T * c + r * (N // R)
+                                 for tid in range(w, w + 32)])
+    return sum(wavefronts(a, 16, 16) for a in accesses) / (2 * len(accesses))
+
+
+def test_ragged_stage0_padding_clears_conflicts():
+    rows = ragged_set0_rows()
+    assert set(rows) == set(range(1, 12))
+    for L in range(2, 8):  # the lengths slot_pad pads
+        row = rows[L]
+        T = row["N"] // row["E"]
+        assert ragged_stage0_factor(row, 0) >= 2.0, L          # packed: 2-8 way
+        assert ragged_stage0_factor(row, T) == 1.0, L          # padded by T: none
+        assert row["S"] * (row["N"] + T) <= 128 * 17           # fits the ring slot
+    for L in range(8, 12):  # N >= 256 needs no padding
+        assert ragged_stage0_factor(rows[L], 0) == 1.0, L
