@@ -475,7 +475,8 @@ __device__ __forceinline__ int slot_pad(int log2n) {
     }
 }
 
-// stage-0 inputs from signal `sl` of a tile laid out every `pitch` elements
+// stage-0 inputs of this thread's signal, which starts at element `sb` of the
+// slot (sl * N packed, sl * (N + T) padded); conjugated for the inverse
 template <class C, bool INV>
 __device__ __forceinline__ void slot_gather0(float2 (&v)[C::E], const float2* tile, int sb, int t) {
     constexpr int R = C::radix(0);
