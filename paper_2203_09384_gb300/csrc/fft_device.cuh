@@ -430,6 +430,12 @@ struct Cfg {
     // XB = -3: exchanges in the ring slot and the tensor-core A operand in
     // TMEM (written with tcgen05.st, 16 columns after the accumulators)
     static constexpr bool kAInTmem = XB_ == -3;
+    // XB = -5: as -1, with the tile's signals placed every N + T elements of
+    // the ring slot (one bulk copy per signal, issued by the lanes of warp 0):
+    // stage 0, which reads the slot as the copies wrote it, then meets no
+    // bank conflicts (packed, the signals all start on the same banks); the
+    // exchanges use the dense layout behind the barrier that follows stage 0
+    static constexpr bool kPadSlot = XB_ == -5;
     // exchange buffers: one suffices when a signal stays in one warp; across
     // warps two let one barrier per exchange do (XB = 1 forces one buffer and
     // a second barrier, halving the shared memory of the exchange)
@@ -439,7 +445,9 @@ struct Cfg {
     static constexpr bool kShuffle = XB_ == 3;
     static constexpr int kBuffers = kInRing ? 1 : kShuffle ? 0 : XB_ ? XB_ : (kWarpLocal ? 1 : 2);
     static constexpr int kSmemElems = kInRing ? 0 : kBuffers * S * N;  // exchange buffers
-    static constexpr int kRingElems = PIPE * S * N;               // prefetch ring
+    static constexpr int kSlotPad = kPadSlot ? T : 0;             // elements between signals in a slot
+    static constexpr int kSlotElems = S * (N + kSlotPad);         // one ring slot
+    static constexpr int kRingElems = PIPE * kSlotElems;          // prefetch ring
     // 0: FP32 butterflies; 1 / 2: radix-16 stages on FP16 / BF16 tensor cores;
     // + 4: only the last radix-16 stage on tensor cores (one MMA round trip
     // per tile), the others in FP32
@@ -497,6 +505,8 @@ struct Cfg {
                   "shuffle exchange: two stages N = R x R, one butterfly of R per thread, R lanes per signal");
     static_assert(!kAInRing || TC == 0 || kTcTiles * 8192 <= S * N * 8, "the A operand must fit in a ring slot");
     static_assert(!kAInTmem || TC == 0 || kTcTiles == 1, "A in TMEM: one 128-row tile per block");
+    static_assert(!kPadSlot || (TC_ == 0 && (N + T) % 2 == 0),
+                  "padded slots: FP32, every signal on a 16-byte boundary");
     // a signal spanning warps finds its maximum through shared memory after a
     // block barrier, so its first stage cannot be a tensor-core one
     static_assert(!kTcSignalScale || (R0 != 16 && PIPE >= 2 && NT <= 256),
@@ -1096,7 +1106,7 @@ __device__ __forceinline__ void gather_tile(float2 (&v)[C::E], const float2* til
         const int j = bfly<C, 0>(t, c);
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            if (!dbg_ok(sb + j + r * stride < C::S * C::N)) continue;
+            if (!dbg_ok(sb + j + r * stride < C::kSlotElems)) continue;
             float2 a = tile[sb + j + r * stride];
             v[c * R + r] = INV ? conj2(a) : a;
         }
@@ -1230,7 +1240,7 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
                                   float scale, int* err, uint64_t wait_ns, int stall) {
     static_assert(C::kInRing, "in-ring schedules only");
     constexpr int D = C::PIPE;
-    constexpr int TILE = C::S * C::N;
+    constexpr int TILE = C::kSlotElems;
     extern __shared__ __align__(16) float2 smem[];
     float2* ring = smem;
     uint64_t* bars = reinterpret_cast<uint64_t*>(ring + D * TILE);
@@ -1242,16 +1252,32 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
     dbg_set_err(err);
 
     RingInFlight inflight;  // thread 0's copies in flight
-    // copy the tile of the block's iteration `j` into slot j mod D (thread 0 only)
+    // copy the tile of the block's iteration `j` into slot j mod D: thread 0
+    // with one copy, or (padded slots) the lanes of warp 0 with one copy per
+    // signal after lane 0 has set the byte count
+    constexpr int kIssuers = C::kPadSlot ? 32 : 1;
     auto issue = [&](int64_t j) {
         const int slot = (int)(j % D);
         const int64_t tile = blockIdx.x + j * gridDim.x;
         const int64_t first = tile * C::S;
         const int64_t left = batch - first;
-        const uint32_t bytes = (uint32_t)((left < C::S ? left : C::S) * C::N * 8);
-        mbar_arrive_expect_tx(&bars[slot], bytes);
-        bulk_copy_g2s(ring + slot * TILE, in + first * C::N, bytes, &bars[slot]);
-        inflight.issued(slot, (uint32_t)((j / D) & 1));
+        const int nsig = (int)(left < C::S ? left : C::S);
+        const uint32_t bytes = (uint32_t)(nsig * C::N * 8);
+        if constexpr (C::kPadSlot) {
+            const int lane = threadIdx.x & 31;
+            if (lane == 0) {
+                mbar_arrive_expect_tx(&bars[slot], bytes);
+                inflight.issued(slot, (uint32_t)((j / D) & 1));
+            }
+            __syncwarp();
+            for (int q = lane; q < nsig; q += 32)
+                bulk_copy_g2s(ring + slot * TILE + q * (C::N + C::kSlotPad), in + (first + q) * C::N,
+                              (uint32_t)(C::N * 8), &bars[slot]);
+        } else {
+            mbar_arrive_expect_tx(&bars[slot], bytes);
+            bulk_copy_g2s(ring + slot * TILE, in + first * C::N, bytes, &bars[slot]);
+            inflight.issued(slot, (uint32_t)((j / D) & 1));
+        }
     };
     if (tid == 0) {
         for (int d = 0; d < D; ++d) mbar_init(&bars[d], 1);
@@ -1260,7 +1286,7 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
     __syncthreads();
     // stall != 0 is the failure-detection test mode: nothing is issued, so
     // every wait below runs out, records FFT_ERR_TIMEOUT and the kernel ends
-    if (tid == 0 && !stall) {
+    if (tid < kIssuers && !stall) {
         for (int d = 0; d < D; ++d)
             if (blockIdx.x + (int64_t)d * gridDim.x < ntiles) issue(d);
     }
@@ -1288,16 +1314,19 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
         if constexpr (C::kAInRing) tc.a = reinterpret_cast<unsigned char*>(b);
         const int64_t sig = tile * C::S + sl;
         float2 v[C::E];
-        gather_tile<C, INV>(v, b, sb, t);
+        gather_tile<C, INV>(v, b, sl * (C::N + C::kSlotPad), t);
         tc_norm_begin<C>(v, tc);
         twist_and_dft<C, 0>(v, t, tw, tc);
         // order this thread's generic accesses of the previous tile's slot
         // before the bulk copy that refills it, then one barrier: every thread
         // is done with that slot and has read this tile's stage-0 inputs
+        // (padded slots: before the dense exchanges overwrite them)
         fence_proxy_async_smem();
         __syncthreads();
-        if (tid == 0 && it > 0 && !dead && !stall) {
-            if (tile + (int64_t)(D - 1) * gridDim.x < ntiles) issue(it - 1 + D);
+        if (tid < kIssuers && it > 0 && !stall) {
+            bool go = !dead;
+            if constexpr (C::kPadSlot) go = __shfl_sync(0xffffffffu, go, 0);  // warp 0 follows lane 0
+            if (go && tile + (int64_t)(D - 1) * gridDim.x < ntiles) issue(it - 1 + D);
         }
         tc_norm_end<C>(v, tc);  // signals spanning warps: maxima published before the barrier
         scatter<C, 0>(v, b, sb, t);

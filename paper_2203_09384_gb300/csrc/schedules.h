@@ -22,7 +22,9 @@
 //           the tile arrived in; -2 = as -1, and the tensor-core A operand
 //           lives in that slot too; -3 = as -1, with the A operand in TMEM;
 //           3 = none: the exchange of a two-stage N = R x R row with E = R is
-//           a transpose by warp shuffles,
+//           a transpose by warp shuffles; -5 = as -1, with the signals of a
+//           tile placed every N + T elements of the slot (one bulk copy per
+//           signal), so that stage 0 reads them without bank conflicts,
 //      CH = cache hints: bit 0 plain loads, bit 1 plain stores (else
 //           evict-first); the defaults are the measured best per length)
 // Threads per block = S * N / E.  Stage 0 with R0 = E/2 (and the last stage,
@@ -39,10 +41,10 @@
 
 #define GBFFT_GENERIC_SCHEDULES(GX)                   \
     GX(5, 1, 16, 128, 8, 4, 0, 0, 1, 0, 0, 0, 0) \
-    GX(6, 0, 16, 64, 8, 8, 0, 0, 1, 0, 0, 0, 0) \
+    GX(6, 0, 16, 32, 8, 8, 0, 0, 4, 2, 0, -5, 2) \
     GX(6, 2, 8, 32, 8, 8, 0, 0, 1, 0, 0, 3, 0) \
     GX(6, 3, 8, 32, 8, 8, 0, 0, 1, 0, 0, 0, 0) \
-    GX(7, 0, 16, 32, 8, 16, 0, 0, 1, 0, 0, 0, 2) \
+    GX(7, 0, 16, 16, 8, 16, 0, 0, 4, 2, 0, -5, 2) \
     GX(7, 1, 16, 16, 8, 16, 0, 0, 3, 2, 1, 0, 0) \
     GX(7, 2, 16, 16, 8, 16, 0, 0, 3, 2, 2, 0, 0) \
     GX(7, 3, 16, 32, 8, 16, 0, 0, 2, 0, 1, 0, 0) \
@@ -95,7 +97,9 @@
     GX(11, 5, 16, 1, 8, 16, 16, 0, 5, 2, 2, -3, 2) \
     GX(11, 17, 16, 1, 8, 16, 16, 0, 5, 2, 5, -3, 2) \
     GX(11, 18, 16, 1, 8, 16, 16, 0, 5, 2, 6, -3, 2) \
-    GX(11, 19, 16, 1, 8, 16, 16, 0, 5, 2, 0, -1, 2)
+    GX(11, 19, 16, 1, 8, 16, 16, 0, 5, 2, 0, -1, 2) \
+    GX(6, 4, 16, 64, 8, 8, 0, 0, 1, 0, 0, 0, 0) \
+    GX(7, 6, 16, 32, 8, 16, 0, 0, 1, 0, 0, 0, 2)
 
 #define GBFFT_SMALL_SCHEDULES(SX) \
     SX(1, 0, 8, 1, 3)                \

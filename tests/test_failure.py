@@ -26,10 +26,11 @@ TIMEOUT = _abi.STATUS_CODE["FFT_ERR_TIMEOUT"]
 # default FP32 schedule, at N = 1024 / 2048 the default tensor-core schedules
 # and variant 11 (FP16) are ring kernels that exchange inside the ring slot;
 # variant 10 of N = 2048 is the ring kernel with two exchange buffers and
-# variant 13 the one with one separate exchange buffer.
+# variant 13 the one with one separate exchange buffer; the N = 64 and 128
+# defaults place their signals apart in the ring slot (copies by warp 0).
 @pytest.mark.parametrize("n,dtype,variant", [(2048, "c64", None), (1024, "c64", None), (256, "tc_f16", None),
                                              (2048, "tc_bf16", None), (2048, "c64", 10), (1024, "tc_f16", 11),
-                                             (2048, "tc_f16", 13)])
+                                             (2048, "tc_f16", 13), (64, "c64", None), (128, "c64", None)])
 def test_bounded_wait_reports_timeout(n, dtype, variant):
     batch = 4 * 152 + 3
     x = synth.uniform(batch, n, seed=1).cuda()
@@ -118,8 +119,9 @@ def test_ragged_variants_without_waits_ignore_the_test_flag(variant):
 
 
 def test_kernels_without_waits_ignore_the_test_flag():
-    x = synth.uniform(100, 64, seed=2).cuda()
-    plan = gb.Plan(64, 100, extra_flags=gb.FFT_FLAG_TEST_STALL)
+    x = synth.uniform(100, 512, seed=2).cuda()
+    plan = gb.Plan(512, 100, extra_flags=gb.FFT_FLAG_TEST_STALL)  # the direct kernel: no device waits
+    assert plan.info().pipeline == 0
     y = plan.execute(x)
     torch.cuda.synchronize()
     assert plan.error() == 0

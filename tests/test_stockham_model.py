@@ -21,7 +21,8 @@ from tests.test_bank_model import _rows, swz8
 def all_rows():
     rows = []
     for L, v, E, S, r0, r1, r2, r3, minb, pipe, tc, xb, ch in _rows("GBFFT_GENERIC_SCHEDULES", 13):
-        rows.append(("GX" if xb != 3 else "GX-shuffle", L, v, E, S, [r for r in (r0, r1, r2, r3) if r], pipe))
+        kind = "GX-shuffle" if xb == 3 else "GX-padded" if xb == -5 else "GX"
+        rows.append((kind, L, v, E, S, [r for r in (r0, r1, r2, r3) if r], pipe))
     for L, v, E, S, r0, r1, r2, r3, minb, pipe, xb in _rows("GBFFT_C32_SCHEDULES", 11):
         rows.append(("CX", L, v, E, S, [r for r in (r0, r1, r2, r3) if r], pipe))
     return rows
@@ -58,10 +59,12 @@ def shuffle_transpose(v, plant=None):
     return v
 
 
-def replay(N, E, S, radix, pipe, x, plant=None, shuffle=False):
+def replay(N, E, S, radix, pipe, x, plant=None, shuffle=False, pad=0):
     """x: [S, N] complex; returns the tile's output [S, N] as the kernel
     computes it (exact arithmetic in complex128).  `plant` puts one plausible
-    mistake into the mapping, to show the replay can fail."""
+    mistake into the mapping, to show the replay can fail.  `pad`: the ring
+    slot holds signal q at element q (N + pad), as the per-signal copies of a
+    padded in-ring schedule write it (XB = -5), and stage 0 reads it there."""
     T = N // E
     NT = T * S
     M = len(radix)
@@ -75,11 +78,13 @@ def replay(N, E, S, radix, pipe, x, plant=None, shuffle=False):
             return K * t + c
         return t + T * c
 
-    flat = x.reshape(-1)
+    flat = np.full(S * (N + pad), np.nan + 0j)  # the slot as the copies write it
+    for q in range(S):
+        flat[q * (N + pad):q * (N + pad) + N] = x[q]
     v = np.zeros((NT, E), dtype=np.complex128)
     R, K, stride = radix[0], E // radix[0], N // radix[0]
     for tid in range(NT):
-        sb, t = (tid // T) * N, tid % T
+        sb, t = (tid // T) * (N + pad), tid % T
         for c in range(K):
             j = bfly(0, t, c)
             for r in range(R):
@@ -144,7 +149,7 @@ def test_schedule_row_computes_the_dft(row):
     assert int(np.prod(radix)) == N and all(E % r == 0 for r in radix)
     rng = np.random.default_rng(L * 100 + variant)
     x = rng.standard_normal((S, N)) + 1j * rng.standard_normal((S, N))
-    y = replay(N, E, S, radix, pipe, x, shuffle=kind == "GX-shuffle")
+    y = replay(N, E, S, radix, pipe, x, shuffle=kind == "GX-shuffle", pad=N // E if kind == "GX-padded" else 0)
     assert not np.isnan(y).any(), "an output element was never stored"
     assert np.allclose(y, np.fft.fft(x, axis=1), rtol=0, atol=1e-9 * N)
 
