@@ -243,9 +243,10 @@ __device__ __forceinline__ void st_stream4v(float4* p, float4 a) {
 // `row = a >> 4` are XOR-permuted by the row index, for transforms of length
 // N = 32 and 64 by row ^ (row >> 2).  By the row alone their exchanges
 // (signals starting every 2 or 4 rows) take 1.5x the conflict-free
-// wavefronts; with row >> 2 folded in none conflicts.  Every other length is
-// conflict free (or at its bound) either way and keeps the cheaper form:
-// measured, the folded form cost the N = 2048 ring kernel 1.4 points.
+// wavefronts; with row >> 2 folded in none conflicts.  The other lengths keep
+// the cheaper form (measured, the folded one cost the N = 2048 ring kernel
+// 1.4 points); their defaults model at 1.0x, except N = 512 (1.25x) and the
+// exchanges of the N = 128 padded in-ring default (1.33x).
 // tests/test_bank_model.py replays every schedule's exchanges under it and
 // counts the wavefronts (64-bit accesses resolve per half-warp), in agreement
 // with ncu.
