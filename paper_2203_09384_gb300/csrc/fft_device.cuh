@@ -273,6 +273,17 @@ __device__ __forceinline__ int swz16(int a) {
     }
 }
 
+// Programmatic dependent launch.  Every kernel here starts with pdl_enter():
+// it lets the next kernel of its stream launch at once (so that its blocks
+// are scheduled while this grid drains, instead of after it), then waits
+// until the previous kernel of the stream has completed and its memory is
+// visible, before touching any buffer.  Both steps are no-ops for a kernel
+// launched without programmatic stream serialization.
+__device__ __forceinline__ void pdl_enter() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 // ---------------------------------------------------------------------------
 // Bulk copy (TMA, non-tensor form) and mbarrier primitives, inline PTX
 // ---------------------------------------------------------------------------
@@ -1072,6 +1083,7 @@ template <class C, bool INV>
 __global__ void __launch_bounds__(C::NT, C::MINB)
     fft_stockham_kernel(const float2* in, float2* out, int64_t batch, const float2* __restrict__ tw, float scale,
                         int* err, uint64_t wait_ns, int stall) {
+    pdl_enter();
     extern __shared__ __align__(16) float2 smem[];
     const int tid = threadIdx.x;
     const int sl = tid / C::T;
@@ -1124,6 +1136,7 @@ template <class C, bool INV>
 __global__ void __launch_bounds__(C::NT, C::MINB)
     fft_stockham_ring_kernel(const float2* in, float2* out, int64_t batch, const float2* __restrict__ tw,
                              float scale, int* err, uint64_t wait_ns, int stall) {
+    pdl_enter();
     constexpr int D = C::PIPE;
     constexpr int TILE = C::S * C::N;
     extern __shared__ __align__(16) float2 smem[];
@@ -1239,6 +1252,7 @@ template <class C, bool INV>
 __global__ void __launch_bounds__(C::NT, C::MINB)
     fft_stockham_slot_ring_kernel(const float2* in, float2* out, int64_t batch, const float2* __restrict__ tw,
                                   float scale, int* err, uint64_t wait_ns, int stall) {
+    pdl_enter();
     static_assert(C::kInRing, "in-ring schedules only");
     constexpr int D = C::PIPE;
     constexpr int TILE = C::kSlotElems;
@@ -1365,6 +1379,7 @@ struct SmallCfg {
 template <class SC, bool INV>
 __global__ void __launch_bounds__(SC::NT) fft_small_kernel(const float2* in, float2* out, int64_t batch,
                                                            float scale) {
+    pdl_enter();
     constexpr int N = SC::N, H = SC::H, W = SC::WARPS_PER_BLOCK, U = SC::UNROLL;
     constexpr int TS = 32 * U;  // signals per warp tile
     extern __shared__ __align__(16) float4 smem4[];
@@ -1552,6 +1567,7 @@ template <class C, bool INV>
 __global__ void __launch_bounds__(C::NT, C::MINB)
     fft_stockham_c32_kernel(const __half2* in, const int8_t* in_exp, __half2* out, int8_t* out_exp, int64_t batch,
                             const float2* __restrict__ tw, float scale, int* err, uint64_t wait_ns, int stall) {
+    pdl_enter();
     extern __shared__ __align__(16) float2 smem[];
     float* red = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(smem) + C32Smem<C>::kRedOffset);
     const int tid = threadIdx.x;
@@ -1602,6 +1618,7 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
     fft_stockham_c32_ring_kernel(const __half2* in, const int8_t* in_exp, __half2* out, int8_t* out_exp,
                                  int64_t batch, const float2* __restrict__ tw, float scale, int* err,
                                  uint64_t wait_ns, int stall) {
+    pdl_enter();
     constexpr int D = C::PIPE;
     constexpr int TILE = C::S * C::N;
     using SM = C32Smem<C>;
@@ -1692,6 +1709,7 @@ template <class SC, bool INV>
 __global__ void __launch_bounds__(SC::NT)
     fft_small_c32_kernel(const __half2* in, const int8_t* in_exp, __half2* out, int8_t* out_exp, int64_t batch,
                          const float2* __restrict__ tw, float scale, int* err, uint64_t wait_ns, int stall) {
+    pdl_enter();
     constexpr int N = SC::N, W = SC::WARPS_PER_BLOCK, U = SC::UNROLL;
     constexpr int TS = 32 * U;         // signals per warp tile
     constexpr int P = TS * N / 4;      // 128-bit pieces per warp tile

@@ -229,6 +229,7 @@ __device__ __forceinline__ void ragged_dispatch(const RaggedArgs& a, const Ragge
 // so the data loads of an item start without a chain of dependent reads.
 template <int V, bool INV>
 __global__ void __launch_bounds__(kRaggedThreads, RaggedMinBlocks<V & 1>::value) fft_ragged_kernel(RaggedArgs a) {
+    pdl_enter();
     constexpr int S = V & 1;  // schedule set
     extern __shared__ __align__(16) float2 smem[];
     dbg_set_err(a.err);
@@ -312,6 +313,7 @@ __device__ __forceinline__ void ragged_ring_tile(const RaggedArgs& a, const Ragg
 // signals in flight into the other ring slot while the current one runs.
 template <bool INV>
 __global__ void __launch_bounds__(kRaggedThreads, 3) fft_ragged_ring_kernel(RaggedArgs a) {
+    pdl_enter();
     extern __shared__ __align__(16) float2 smem[];
     float2* xbuf = smem;                   // 2 exchange buffers
     float2* ring = smem + 2 * kRingTile;   // 2 ring slots
@@ -661,6 +663,7 @@ __device__ __forceinline__ void ragged_slot_body(const RaggedArgs& a) {
 template <int NTC, int SLOTS, int MINB, bool INV>
 __global__ void __launch_bounds__(SlotShape<NTC, MINB>::kThreads, SlotShape<NTC, MINB>::kMinBlocks)
     fft_ragged_slot_kernel(RaggedArgs a) {
+    pdl_enter();
     ragged_slot_body<NTC, SLOTS, MINB, 0, INV>(a);
 }
 
@@ -671,6 +674,7 @@ __global__ void __launch_bounds__(SlotShape<NTC, MINB>::kThreads, SlotShape<NTC,
 // no faster.)
 template <int NTC, int SLOTS, int REGS, int CH, bool INV>
 __global__ void __maxnreg__(REGS) fft_ragged_slot_kernel_capped(RaggedArgs a) {
+    pdl_enter();
     ragged_slot_body<NTC, SLOTS, 5, CH, INV>(a);
 }
 
@@ -956,9 +960,9 @@ fft_status_t ragged_execute(RaggedState* st, const void* in, void* out, void* st
     args.in = static_cast<const float2*>(in);
     args.out = static_cast<float2*>(out);
     void* kargs[] = {&args};
-    if (cudaLaunchKernel(ragged_kernel(st->variant, st->inverse), dim3((unsigned)st->grid),
-                         dim3(ragged_threads(st->variant)),
-                         kargs, (size_t)st->smem, s) != cudaSuccess) {
+    if (launch_kernel(ragged_kernel(st->variant, st->inverse), (unsigned)st->grid,
+                      (unsigned)ragged_threads(st->variant), kargs, (size_t)st->smem, s,
+                      st->end - st->begin) != cudaSuccess) {
         cudaGetLastError();
         return FFT_ERR_CUDA;
     }

@@ -102,6 +102,22 @@ namespace {
 thread_local int t_plan_allocs = 0;
 }
 void begin_plan_allocs() { t_plan_allocs = 0; }
+cudaError_t launch_kernel(const void* kernel, unsigned grid, unsigned block, void** args, size_t smem,
+                          cudaStream_t stream, int64_t elems) {
+    if (elems < kPdlMinElems) return cudaLaunchKernel(kernel, dim3(grid), dim3(block), args, smem, stream);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelExC(&cfg, kernel, args);
+}
+
 cudaError_t plan_malloc(void** ptr, size_t bytes) {
     ++t_plan_allocs;
     const char* fail = getenv("GBFFT_TEST_FAIL_ALLOC");
@@ -163,13 +179,13 @@ fft_status_t launch_plain(gbfft_plan* p, const float2* in2, float2* out2, int64_
     cudaError_t ce;
     if (e->kind == KernelKind::Small) {
         void* args[] = {&in2, &out2, &batch, &scale};
-        ce = cudaLaunchKernel(p->kernel, dim3((unsigned)grid), dim3(e->threads_per_block), args,
-                              (size_t)e->smem_bytes, stream);
+        ce = gbfft::launch_kernel(p->kernel, (unsigned)grid, (unsigned)e->threads_per_block, args,
+                                  (size_t)e->smem_bytes, stream, batch * p->n);
     } else {
         int stall = (p->flags & FFT_FLAG_TEST_STALL) ? 1 : 0;
         void* args[] = {&in2, &out2, &batch, &tw, &scale, &err, &wait_ns, &stall};
-        ce = cudaLaunchKernel(p->kernel, dim3((unsigned)grid), dim3(e->threads_per_block), args,
-                              (size_t)e->smem_bytes, stream);
+        ce = gbfft::launch_kernel(p->kernel, (unsigned)grid, (unsigned)e->threads_per_block, args,
+                                  (size_t)e->smem_bytes, stream, batch * p->n);
     }
     if (ce != cudaSuccess) {
         cudaGetLastError();
@@ -504,8 +520,8 @@ fft_status_t fft_execute_c32(fft_plan_t p, const void* in, const int8_t* in_exp,
     uint64_t wait_ns = p->wait_ns;
     int stall = (p->flags & FFT_FLAG_TEST_STALL) ? 1 : 0;
     void* args[] = {&in2, &in_exp, &out2, &out_exp, &batch, &tw, &scale, &err, &wait_ns, &stall};
-    if (cudaLaunchKernel(p->kernel, dim3((unsigned)p->grid), dim3(e->threads_per_block), args,
-                         (size_t)e->smem_bytes, (cudaStream_t)stream) != cudaSuccess) {
+    if (gbfft::launch_kernel(p->kernel, (unsigned)p->grid, (unsigned)e->threads_per_block, args,
+                             (size_t)e->smem_bytes, (cudaStream_t)stream, batch * p->n) != cudaSuccess) {
         cudaGetLastError();
         return FFT_ERR_CUDA;
     }

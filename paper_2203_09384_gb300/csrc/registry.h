@@ -42,6 +42,15 @@ struct KernelEntry {
 // allocation-failure path of plan creation.
 void begin_plan_allocs();
 cudaError_t plan_malloc(void** ptr, size_t bytes);
+// Every kernel launch of the library.  A call that moves at least
+// kPdlMinElems elements is launched with programmatic stream serialization,
+// so that it may be scheduled while the previous kernel of the stream drains
+// (each kernel waits for its predecessor before touching memory, pdl_enter);
+// smaller calls are bound by the host's launch rate, where the extended
+// launch only adds host time.
+constexpr int64_t kPdlMinElems = int64_t(1) << 22;
+cudaError_t launch_kernel(const void* kernel, unsigned grid, unsigned block, void** args, size_t smem,
+                          cudaStream_t stream, int64_t elems);
 
 // Registry lookup (host): the entry of `variant`, or of the length's current
 // default when variant < 0; NULL when there is none.
