@@ -162,6 +162,10 @@ GBFFT_API fft_status_t fft_plan_create_ex(int64_t n, int64_t batch, int directio
  * any other overlap is rejected.  Both pointers must be 16-byte aligned.
  * The caller owns both buffers and must keep them alive until the stream has
  * run the kernel.  One plan may be executed concurrently on several streams.
+ * A call of 2^22 elements or more is launched with programmatic stream
+ * serialization: its kernel may be scheduled while the previous kernel of the
+ * stream finishes, but it waits for that kernel to complete before it reads or
+ * writes any buffer, so stream order holds as for a plain launch.
  * Errors: FFT_ERR_INVALID_VALUE, FFT_ERR_MISALIGNED, FFT_ERR_OVERLAP,
  * FFT_ERR_CUDA (launch failure, reported from cudaGetLastError).
  */
