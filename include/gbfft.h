@@ -128,7 +128,7 @@ GBFFT_API fft_status_t fft_plan_create(int64_t n, int64_t batch, int direction, 
  * FFT_FLAG_VARIANT(k) with k < fft_ragged_variant_count() (without it: the
  * process-wide default of fft_set_default_ragged_variant, initially variant
  * 9: a producer warp filling ring slots for 128 compute threads per block,
- * five blocks per SM, the lengths up to 64 first in the work list).
+ * four such blocks per SM, the lengths up to 128 first in the work list).
  * Errors: FFT_ERR_INVALID_SIZE (a length), FFT_ERR_INVALID_VALUE, FFT_ERR_MISALIGNED
  * (odd offsets_host[0]), FFT_ERR_ALLOC, FFT_ERR_CUDA, FFT_ERR_NO_DEVICE.
  */

@@ -5,7 +5,7 @@
 // tiles of S_N signals (the same per-length schedules as the uniform path,
 // re-shaped so that every length runs in a 256-thread block), and the tiles
 // become a device work list ordered from the longest length down (variant 9:
-// the lengths up to 64 first, then the rest longest first).
+// the lengths up to 128 first, then the rest longest first).
 //
 // Ten variants are compiled.  Bit 0 of variants 0..3 picks the schedule
 // set: set 0 keeps 16 complex elements per thread for N >= 32 (fewest
@@ -18,7 +18,7 @@
 // (exchanges inside the slot): 5 with 256 compute threads and 2 slots, 6 with
 // 128 compute threads and 2 slots, 7 with 128 and 3 slots, 8 as 6 with
 // registers capped at 80, 9 (the default) the kernel of 8 with the lengths up
-// to 64 first in the work list.
+// to 128 first in the work list.
 // A tile whose signals lie back to back (runs of one length in the input)
 // is marked at plan time: its threads compute their offsets instead of
 // loading them, and the bulk-copy variants fetch a tile of short signals in
@@ -118,7 +118,7 @@ constexpr int kRingVariant = 4;
 constexpr int kFirstProducerVariant = 5;
 constexpr int kDefaultRaggedVariant = 9;  // measured fastest on the mixed-length workload
 constexpr int kShortFirstVariant = 9;     // variant 8's kernel, short lengths first in the work list
-constexpr int kShortMaxLog2n = 6;
+constexpr int kShortMaxLog2n = 7;  // measured: up to 128 first beats up to 32 or 64 on the mix
 // the variant ragged plans use when the caller names none (process-wide; the
 // autotuner's cached choice is applied through fft_set_default_ragged_variant)
 std::atomic<int> g_default_ragged_variant{kDefaultRaggedVariant};
@@ -844,9 +844,9 @@ fft_status_t ragged_create(const int64_t* offsets, int64_t count, int direction,
 
     // work list and the bucketed offsets.  Longest length first, so that the
     // last items, which run while the machine drains, are short; variant 9
-    // takes the lengths up to 64 (tiles of many tiny signals, one bulk copy
+    // takes the lengths up to 128 (tiles of many short signals, one bulk copy
     // each) first instead, then the rest longest first, so the final items
-    // are tiles of 8-16 medium signals.  (The named barriers of the producer
+    // are the N = 256 tiles (8 signals each).  (The named barriers of the producer
     // variants allow any order, see slot_sync.)
     std::vector<int> order;
     const bool short_first = variant >= kShortFirstVariant;
